@@ -1,0 +1,87 @@
+"""Plant mistakes in a copy of the oracle (on the CPU) and check that the pins catch them.
+
+Each mutant is oracle.c with one plausible slip; it is compiled into a scratch
+directory and loaded through the same Python wrapper.  The pins used here are
+the star-graph example of Section 4.2, Property 1's column sums, the cycle's
+spectral closed form, Lemma 2 at alpha = 0.2 and the dense solve.
+"""
+import ctypes
+import importlib.util
+import math
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+ORACLE_DIR = os.path.dirname(os.path.abspath(O.__file__))
+
+MUTANTS = {
+    # r_{k+1} = 2 P r_k + r_{k-1}
+    "sign_of_rkm1": ("2.0 * pr[u] - r", "2.0 * pr[u] + r"),
+    # D^-1 A instead of A D^-1 (divide by the row's degree)
+    "row_degree": ("s += x[v] / deg_of(row_ptr, v);", "s += x[v] / deg_of(row_ptr, u);"),
+    # c_0 with 2/pi like the other coefficients
+    "c0_weight": ("c[k] = (k == 0 ? 1.0 : 2.0) / OR_PI * integral;", "c[k] = 2.0 / OR_PI * integral;"),
+    # the last term c_K r_K dropped
+    "drop_last_term": ("for (int64_t u = 0; u < n; ++u) y[u] += c[K] * rcur[u];\n  free(rprev); free(rcur); free(pr);\n  return 0;\n}\n\n/* Algorithm 3 with",
+                       "free(rprev); free(rcur); free(pr);\n  return 0;\n}\n\n/* Algorithm 3 with"),
+}
+
+
+def _load_mutant(tmp_path, name):
+    src = open(os.path.join(ORACLE_DIR, "oracle.c")).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) >= 1, name
+    d = tmp_path / name / "oracle"
+    d.mkdir(parents=True)
+    (d / "oracle.c").write_text(src.replace(old, new))  # every occurrence
+    shutil.copy(os.path.join(ORACLE_DIR, "__init__.py"), d / "__init__.py")
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{name}", d / "__init__.py")
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _pins_hold(M):
+    """True when every pin below holds for module M."""
+    ok = True
+    star = gg.from_edges(4, [(0, 1), (0, 2), (0, 3)])
+    R = M.cheb_basis(star, 1, 3)
+    ok &= np.allclose(R[2], [0, -1 / 3, 2 / 3, 2 / 3], atol=1e-14)
+    ok &= np.allclose(R[3], [1, 0, 0, 0], atol=1e-14)
+    # Algorithm 3 with K = 3 on the star: sum_k c_k r_k with the example's exact r_k.
+    c3 = [1 / 3, 1 / 3, 1 / 6, 1 / 12]  # Lemma 2 at alpha = 0.2
+    r = [[0, 1, 0, 0], [1, 0, 0, 0], [0, -1 / 3, 2 / 3, 2 / 3], [1, 0, 0, 0]]
+    want3 = sum(ck * np.array(rk) for ck, rk in zip(c3, r))
+    ok &= np.allclose(M.chebypower(star, 1, "ppr", 0.2, 3, coeffs=np.array(c3)), want3, atol=1e-15)
+    g = gg.rmat(9, 16, seed=9)
+    s = int(gg.sources(g, 1, 3)[0])
+    ok &= bool(np.max(np.abs(M.cheb_basis(g, s, 20).sum(axis=1) - 1.0)) < 1e-9)
+    c = M.cheb_coeffs("ppr", 0.2, 10)
+    ok &= abs(c[0] - 1 / 3) < 1e-13 and abs(c[1] - 1 / 3) < 1e-13
+    n = 64
+    cyc = gg.from_edges(n, [(i, (i + 1) % n) for i in range(n)])
+    j = np.arange(n)
+    fl = M.gp_f("ppr", 0.2, np.cos(2 * np.pi * j / n))
+    want = np.array([np.sum(fl * np.cos(2 * np.pi * j * (u - 5) / n)) / n for u in range(n)])
+    ok &= bool(np.max(np.abs(M.chebypower(cyc, 5, "ppr", 0.2, 80) - want)) < 1e-12)
+    ok &= bool(np.max(np.abs(M.chebypower(g, s, "ppr", 0.2, 80) - M.dense_ppr(g, s, 0.2))) < 1e-12)
+    return bool(ok)
+
+
+def test_unmutated_oracle_passes_pins():
+    assert _pins_hold(O)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    M = _load_mutant(tmp_path, name)
+    assert not _pins_hold(M), f"mutant {name} passed every pin"
