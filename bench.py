@@ -1,0 +1,367 @@
+"""Benchmark: single-source ChebyPower queries/s on R-MAT scale 22.
+
+Workload (the headline configuration): seeded R-MAT graph, scale 22
+(4,194,304 nodes), edge factor 16, (a, b, c) = (0.57, 0.19, 0.19), symmetrised
+without self-loops or duplicates (128.3M directed entries), int32 CSR.  One
+step = 64 uniformly random sources (degree >= 1), each queried one at a time as
+SSPPR (alpha = 0.2) and as HKPR (t = 5), l1 tolerance 1e-6, FP32 storage with
+compensated FP32 sums and float-pair accumulation, float64 output.  Inputs are
+larger than L2 (the 513 MB col_idx stream), so no L2 flush is needed between
+steps.
+
+`value` is device-resident throughput (outputs stay in HBM); `e2e` is the same
+metric through the public C ABI with host (pinned) output buffers, the
+device-to-host copy of every result inside the timed region.  `roofline` is the
+fused step kernel's algorithmic bytes per launch over its mean CUDA-event
+duration, against the measured HBM copy bandwidth.  `cpu_baseline` times the
+FP64 oracle on the host cores on a bounded sample of the same workload.
+
+Multi-GPU: queries are independent, so N GPUs run N replicas of the graph
+with the same per-GPU work (weak scaling, no data-path collective).
+`--impl reference` times the FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "PPR/HKPR queries/s at l1<=1e-6 (single-source ChebyPower, R-MAT scale 22)"
+UNIT = "queries/s"
+PROFILE_FILE = os.path.join(ROOT, "profiles", "cheb_step_rmat22.json")
+STEP_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2412_10789_gb300", "csrc", f)
+                       for f in ("cheb.cu", "gp_internal.h")]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=int, default=22)
+    p.add_argument("--sources", type=int, default=64)
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--power-baseline", action="store_true", help="also time the GPU PwMethod")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- distributed helpers
+
+def dist_setup(args):
+    """(rank, world) from torchrun's environment; NCCL process group when world > 1."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def dist_max(x: float, world: int, device=None) -> float:
+    """Max of a scalar over ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- workload
+
+def workload(scale, nsrc):
+    import graphgen as gg
+    g = gg.rmat(scale, 16, 0.57, 0.19, 0.19, seed=2)
+    srcs = gg.sources(g, nsrc, 2)
+    queries = [(0, int(s), 0.2) for s in srcs] + [(1, int(s), 5.0) for s in srcs]
+    # interleave SSPPR and HKPR
+    queries = [q for pair in zip(queries[:nsrc], queries[nsrc:]) for q in pair]
+    return g, queries
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in STEP_KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """dram bytes per launch of the step kernel from the committed ncu summary,
+    or None when absent or taken on different kernel source."""
+    try:
+        with open(PROFILE_FILE) as f:
+            prof = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if prof.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return prof.get("dram_bytes_per_launch_full_size")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+
+def time_oracle(g, queries, tol, seconds):
+    """The FP64 oracle (Algorithm 3 with the same l1 stop reading), as it stands,
+    on the host cores, on the first queries of the workload until `seconds` pass."""
+    import oracle as O
+    t0 = time.perf_counter()
+    done = 0
+    for fn, s, p in queries:
+        O.chebypower_tol(g, s, "ppr" if fn == 0 else "hkpr", p, tol)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, O.num_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        dist_barrier(world)
+        return
+    g, queries = workload(args.scale, args.sources)
+    # each step: one SSPPR and one HKPR query of the workload (a bounded sample)
+    per_step = 2
+    times = []
+    qi = 0
+    total_steps = args.warmup + args.steps
+    import oracle as O
+    threads = O.num_threads()
+    for step in range(total_steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            fn, s, p = queries[qi % len(queries)]
+            qi += 1
+            O.chebypower_tol(g, s, "ppr" if fn == 0 else "hkpr", p, args.tol)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(g, args, per_step_queries=per_step),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} queries per step (SSPPR alpha=0.2 + HKPR t=5, l1 stop 1e-6) "
+                                   f"of the R-MAT scale-{args.scale} workload, FP64 CPU oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    dist_barrier(world)
+
+
+def config_dict(g, args, per_step_queries):
+    return {"workload": f"rmat_s{args.scale}_ef16_single_source", "graph": g.name, "n": g.n, "nnz": g.nnz,
+            "queries_per_step": per_step_queries, "functions": "SSPPR alpha=0.2 + HKPR t=5 per source",
+            "l1_tol": args.tol, "storage": "fp32 (compensated sums, float-pair y)", "out": "float64",
+            "l2": "inputs larger than L2 (col_idx 4*nnz bytes), no flush", "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------- GPU leg
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2412_10789_gb300 import build, gp
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        build.build()
+    dist_barrier(world)
+    g, queries = workload(args.scale, args.sources)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
+    ys = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+
+    def one_step(outs, host=False):
+        for i, (fn, s, p) in enumerate(queries):
+            y = outs[i % len(outs)]
+            if fn == 0:
+                gp.gp_ppr(dg, s, p, args.tol, y, info=host)
+            else:
+                gp.gp_hkpr(dg, s, p, args.tol, y, info=host)
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        one_step(ys)
+    torch.cuda.synchronize()
+    # ---- timed region (device-resident outputs)
+    sampler = ClockSampler(local)
+    sampler.start()
+    gp.gp_profile_enable(dg, True)
+    gp.gp_profile_read(dg)
+    launches0 = gp.gp_launch_count()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step(ys)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist_barrier(world)
+    launches = gp.gp_launch_count() - launches0
+    prof = gp.gp_profile_read(dg)
+    gp.gp_profile_enable(dg, False)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = dist_max(ms, world, dev)
+    nq = len(queries) * args.steps * world
+    value = nq / (ms / 1000.0)
+    # ---- e2e: public API, host pinned outputs, D2H inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hs = [torch.empty(g.n, dtype=torch.float64).pin_memory() for _ in range(2)]
+        one_step(hs)
+        dist_barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(hs, host=True)
+        torch.cuda.synchronize()
+        dt = dist_max(time.perf_counter() - t0, world, dev)
+        e2e = {"value": nq / dt, "unit": UNIT,
+               "h2d_bytes_per_step": len(queries) * (4 + 8 + 8),
+               "d2h_bytes_per_step": len(queries) * g.n * 8}
+    # ---- optional GPU PwMethod baseline on the same queries
+    power = None
+    if args.power_baseline:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for fn, s, p in queries:
+            gp.gp_power(dg, fn, s, p, args.tol, ys[0], info=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        power = {"value": len(queries) / dt, "unit": UNIT, "what": "Algorithm 1 on the same GPU, same queries"}
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        done, dt, threads = time_oracle(g, queries, args.tol, args.cpu_seconds)
+        cpu = {"value": done / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {done} queries of the workload (alternating SSPPR/HKPR, l1 stop {args.tol:g}) "
+                         f"in {dt:.1f} s, FP64 CPU oracle, OpenMP over rows"}
+    peak, peak_kind = measured_peaks()
+    mean_launch_ms = prof["step_ms"] / max(prof["step_launches"], 1)
+    bytes_per_launch = prof["step_bytes"] / max(prof["step_launches"], 1)
+    achieved = bytes_per_launch / (mean_launch_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(), "peak_kind": peak_kind, "kernel": "cheb_step_kernel",
+                "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_launch_ms,
+                "launches": prof["step_launches"]}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(g, args, per_step_queries=len(queries)),
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        if power:
+            out["gpu_power_baseline"] = power
+        print(json.dumps(out), flush=True)
+    dg.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -26,13 +26,18 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile gen.cpp into libgraphgen.so (skipped when the library is newer)."""
-    if (not force and os.path.exists(_LIB)
+    import platform
+    stamp = _LIB + ".machine"
+    same = os.path.exists(stamp) and open(stamp).read().strip() == platform.machine()
+    if (not force and same and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
+    with open(stamp, "w") as f:
+        f.write(platform.machine() + "\n")
     return _LIB
 
 

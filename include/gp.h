@@ -1,0 +1,216 @@
+/*
+ * gp.h -- C ABI of the GB300 ChebyPower library (graph propagation by the
+ * Chebyshev power iteration of arXiv 2412.10789).
+ *
+ * What the library computes.  For an undirected graph G = (V, E) with n nodes,
+ * adjacency A, degrees d_u and the random-walk matrix P = A D^{-1} (Section 2.1),
+ * a query asks for the GP vector y = f(P) e_s (Eq. 1) of one source s, where f is
+ *   SSPPR: f(x) = alpha / (1 - (1 - alpha) x), alpha in (0, 1)   (Def. SSPPR)
+ *   HKPR:  f(x) = exp(-t (1 - x)), t > 0                          (Def. HKPR)
+ * It evaluates the truncated Chebyshev expansion y_K = sum_{k<=K} c_k T_k(P) e_s
+ * (Lemma 1, coefficients of Lemma 2 / Lemma 3) with the three-term recurrence
+ * r_{k+1} = 2 P r_k - r_{k-1} (Eq. res-recurrence, Algorithm 3), accumulating
+ * y += c_k r_k in the same pass.  K is the smallest k >= 1 with
+ * tail(k) * max_{l<=k} ||r_l||_1 <= l1_tol, tail(k) = sum_{l>k} |c_l| (Theorem 1
+ * read for the l1 error with Assumption 1's constant measured on the fly), or
+ * a cap.  A node with d_u = 0 has a zero column in P; an isolated source
+ * returns f(0) e_s.
+ *
+ * Conventions shared by every call.
+ *  - Every call returns a gp_status; GP_OK = 0.  On error the out-parameters
+ *    and caller buffers are left untouched and gp_last_error() (thread-local)
+ *    describes the failure.  No C++ exception crosses the ABI.
+ *  - Pointers: "host" pointers are ordinary CPU memory; "device" pointers are
+ *    CUDA global memory of the current device.  Flags named *_on_device say which.
+ *  - The caller keeps ownership of every array it passes in; the library copies
+ *    what it needs.  Output buffers are caller-owned and written only on GP_OK.
+ *  - All work runs on the stream given in gp_config.stream (NULL: a stream the
+ *    library creates for the graph).  A call whose outputs are all on the device
+ *    and that asks for no gp_query_info returns once the work is enqueued
+ *    (stream-ordered); every other call returns after the work has finished.
+ *  - Calls on one gp_graph are serialised by a lock; different graphs are
+ *    independent.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_graph gp_graph; /* opaque; owned by the library */
+
+typedef enum {
+  GP_OK = 0,
+  GP_EINVAL = 1,     /* an argument or the graph failed validation */
+  GP_ENOMEM = 2,     /* device or host allocation failed */
+  GP_ECUDA = 3,      /* a CUDA call failed (message in gp_last_error) */
+  GP_EAGAIN = 4,     /* gp_poll: the query is not finished yet */
+  GP_ENOTFOUND = 5,  /* gp_poll: unknown ticket */
+  GP_ETIMEDOUT = 6,  /* a bounded device-side wait ran out */
+  GP_EBUSY = 7,      /* the serving queue is full */
+  GP_ENOTSUP = 8     /* a combination of options this build does not support */
+} gp_status;
+
+typedef enum { GP_F32 = 0, GP_F64 = 1, GP_BF16 = 2, GP_F16 = 3 } gp_dtype;
+
+typedef enum { GP_FN_PPR = 0, GP_FN_HKPR = 1 } gp_function;
+
+typedef enum {
+  GP_K_TAIL = 0,  /* stop at tail(k) * max_l ||r_l||_1 <= l1_tol (default) */
+  GP_K_PAPER = 1, /* K = ceil(alpha^{-1/2} ln(1/tol)) or ceil(sqrt(t) ln(1/tol)) (Section 6) */
+  GP_K_FIXED = 2  /* K = gp_request.k_fixed */
+} gp_k_rule;
+
+/* Options for a graph; gp_config_default fills the defaults. */
+typedef struct {
+  gp_dtype storage;        /* storage of the T_k blocks in batched / served queries:
+                              GP_F32, GP_BF16 or GP_F16 (16-bit ones with the FP32
+                              warm-up schedule); single queries always use GP_F32 */
+  int32_t block_width;     /* B, columns per batched SpMM pass; 0 = autotune */
+  int32_t autotune;        /* 1: time bucket thresholds / B on this graph at create */
+  int32_t k_max;           /* hard cap on K (default 96) */
+  int32_t validate_symmetry; /* 1 (default): check that every (u,v) has (v,u) */
+  int32_t t_heavy;         /* rows with degree >= t_heavy are summed in pieces by several warps
+                              (0: only rows too long for one whole-row task, > 508 entries) */
+  int32_t row_ptr_64;      /* 1: keep 64-bit row offsets even when nnz fits 32 bits (default 0) */
+  double warmup_tail;      /* 16-bit storage only once tail(k) < warmup_tail (default 1e-2) */
+  size_t mem_budget;       /* bytes the serving loop may use for column blocks (0: 80% of free) */
+  void* (*alloc)(size_t bytes, void* ctx); /* device allocator; NULL: cudaMalloc */
+  void (*free)(void* ptr, void* ctx);      /* its release function */
+  void* alloc_ctx;         /* passed to alloc / free */
+  void* stream;            /* cudaStream_t for all work on this graph; NULL: own stream */
+} gp_config;
+
+/* Per-query report (all fields filled on GP_OK). */
+typedef struct {
+  int32_t K;             /* truncation degree used (number of applications of P) */
+  int32_t k16_from;      /* first step stored in 16 bits (K+1 when none) */
+  double tail_bound;     /* tail(K) * max_{l<=K} ||r_l||_1, the l1 bound of the stop rule */
+  double max_r_l1;       /* max_{l<=K} ||r_l||_1 as measured on the device */
+  double ms;             /* wall time of the query inside the library, milliseconds */
+} gp_query_info;
+
+/* One query for gp_batch / gp_submit. */
+typedef struct {
+  int32_t function;      /* gp_function */
+  int32_t source;        /* 0 <= source < n, in the caller's numbering */
+  double param;          /* alpha (SSPPR) or t (HKPR) */
+  double l1_tol;         /* target l1 error, in (0, 1) */
+  int32_t k_rule;        /* gp_k_rule */
+  int32_t k_fixed;       /* K for GP_K_FIXED */
+  int32_t out_dtype;     /* GP_F64 or GP_F32 */
+  int32_t y_on_device;   /* 1: y_out is device memory, 0: host memory */
+  void* y_out;           /* n elements of out_dtype, caller-owned */
+} gp_request;
+
+/* Fill *cfg with the defaults listed in gp_config. */
+void gp_config_default(gp_config* cfg);
+
+/*
+ * Build a device-resident graph from CSR (Section 2.1: undirected, both
+ * directions stored).  row_ptr has n+1 entries (int32, or int64 when
+ * row_ptr_is_64), col_idx has nnz int32 entries, degree has n int32 entries;
+ * all three are on the device when inputs_on_device, else on the host.
+ * Validation (GP_EINVAL on failure, with the first bad index in the message):
+ * row_ptr[0] = 0, row_ptr[n] = nnz, non-decreasing; 0 <= col_idx < n; rows
+ * strictly increasing (sorted, no duplicates); no self-loops;
+ * degree[u] == row_ptr[u+1] - row_ptr[u] exactly; and, when
+ * cfg->validate_symmetry, every (u, v) has its (v, u).  The library keeps a
+ * relabelled copy (rows ordered by degree, descending, ties by id); results and
+ * sources always use the caller's numbering.  cfg may be NULL.
+ */
+gp_status gp_graph_create(int64_t n, int64_t nnz, const void* row_ptr, int row_ptr_is_64,
+                          const int32_t* col_idx, const int32_t* degree, int inputs_on_device,
+                          const gp_config* cfg, gp_graph** out);
+
+/* Release the graph and everything it owns; waits for queued work and cancels
+ * pending tickets (their gp_poll then reports GP_ENOTFOUND). NULL is accepted. */
+gp_status gp_graph_destroy(gp_graph* g);
+
+/* Sizes of the graph: n, nnz, nodes with degree >= 1, the largest degree. Any
+ * pointer may be NULL. */
+gp_status gp_graph_info(const gp_graph* g, int64_t* n, int64_t* nnz, int64_t* n_active,
+                        int64_t* max_degree);
+
+/* Copy the stored graph back in the caller's numbering (host buffers: row_ptr
+ * n+1 int64, col_idx nnz int32, degree n int32).  A lossless ingest returns the
+ * input arrays bit for bit. */
+gp_status gp_graph_export(const gp_graph* g, int64_t* row_ptr, int32_t* col_idx, int32_t* degree);
+
+/*
+ * SSPPR query (Def. SSPPR; Lemma 2 coefficients; Algorithm 3):
+ * y_out = sum_{k<=K} c_k T_k(P) e_source, K by the GP_K_TAIL rule with l1_tol.
+ * out_dtype: GP_F64 or GP_F32; y_out holds n elements (device memory when
+ * y_on_device).  alpha in (0,1), l1_tol in (0,1), 0 <= source < n, else GP_EINVAL.
+ * info may be NULL.
+ */
+gp_status gp_ppr(gp_graph* g, int32_t source, double alpha, double l1_tol, gp_dtype out_dtype,
+                 void* y_out, int y_on_device, gp_query_info* info);
+
+/* HKPR query (Def. HKPR; Lemma 3 coefficients; Algorithm 3); t > 0.  Otherwise as gp_ppr. */
+gp_status gp_hkpr(gp_graph* g, int32_t source, double t, double l1_tol, gp_dtype out_dtype,
+                  void* y_out, int y_on_device, gp_query_info* info);
+
+/* A single query with every option of gp_request (k rule, fixed K). */
+gp_status gp_query(gp_graph* g, const gp_request* req, gp_query_info* info);
+
+/*
+ * Baseline: Algorithm 1 (PwMethod) on the device, y = sum_{k<N} zeta_k P^k e_s
+ * with zeta_k of Def. SSPPR / Def. HKPR and N the smallest count whose Taylor
+ * tail sum_{k>=N} zeta_k is <= l1_tol (the tail bounds the l1 error because
+ * ||P^k e_s||_1 = 1).  Same arguments as gp_ppr / gp_hkpr; info->K reports N.
+ */
+gp_status gp_power(gp_graph* g, int32_t function, int32_t source, double param, double l1_tol,
+                   gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info);
+
+/*
+ * Batched queries: the `count` requests are packed as columns of one n x B
+ * block and advanced together by a fused SpMM step (B = cfg.block_width or the
+ * tuned width; more requests run as successive blocks).  Each column keeps its
+ * own function, parameter, coefficients and K, and is retired when its own stop
+ * rule fires.  T_k storage follows cfg.storage.  infos may be NULL, else it
+ * receives `count` reports.
+ */
+gp_status gp_batch(gp_graph* g, int32_t count, const gp_request* reqs, gp_query_info* infos);
+
+/*
+ * Continuous-batching service.  gp_submit queues a request and returns a
+ * ticket at once (GP_EBUSY when the queue is full).  A service thread admits
+ * queued requests into free columns of the running block when a column slot and
+ * the memory for its share of the block are free, advances every active column
+ * one step per fused SpMM pass, retires a column when its stop rule fires
+ * (writing y_out before the ticket completes) and refills the slot.  The
+ * request's y_out must stay valid until gp_poll reports completion.
+ * gp_poll returns GP_OK (and fills info) once the ticket is done, GP_EAGAIN
+ * before that, GP_ENOTFOUND for an unknown or already-collected ticket.
+ */
+gp_status gp_submit(gp_graph* g, const gp_request* req, uint64_t* ticket);
+gp_status gp_poll(gp_graph* g, uint64_t ticket, gp_query_info* info);
+
+/* Serving statistics since the graph was created: completed queries, steps
+ * (fused passes) run, and the mean number of active columns per pass. */
+gp_status gp_serve_stats(gp_graph* g, uint64_t* completed, uint64_t* steps, double* mean_active);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t gp_launch_count(void);
+
+/* Kernel timing: while enabled, the fused Chebyshev step kernels of
+ * gp_ppr / gp_hkpr / gp_query / gp_batch are bracketed by CUDA events on their
+ * stream; gp_profile_read returns the summed device time (ms) and launch count
+ * of the launches that did work since the last read, and resets them. */
+gp_status gp_profile_enable(gp_graph* g, int on);
+gp_status gp_profile_read(gp_graph* g, double* step_ms, int64_t* step_launches,
+                          double* step_bytes);
+
+const char* gp_status_string(gp_status s);
+const char* gp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GP_H */

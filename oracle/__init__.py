@@ -39,7 +39,10 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile oracle.c (plain C, no FMA contraction) into liboracle.so."""
-    if (not force and os.path.exists(_LIB)
+    import platform
+    stamp = _LIB + ".machine"
+    same = os.path.exists(stamp) and open(stamp).read().strip() == platform.machine()
+    if (not force and same and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
@@ -47,6 +50,8 @@ def build(force: bool = False) -> str:
            "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
+    with open(stamp, "w") as f:
+        f.write(platform.machine() + "\n")
     return _LIB
 
 
