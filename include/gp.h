@@ -195,6 +195,26 @@ gp_status gp_poll(gp_graph* g, uint64_t ticket, gp_query_info* info);
  * (fused passes) run, and the mean number of active columns per pass. */
 gp_status gp_serve_stats(gp_graph* g, uint64_t* completed, uint64_t* steps, double* mean_active);
 
+/*
+ * Fixed-K SSPPR / HKPR query that allocates no memory (the paper has no
+ * counterpart; this is for callers that cannot allocate device memory when
+ * they query: a host framework that owns all device memory, or a loop that
+ * cannot afford cudaFree's device-wide synchronisation or a failing
+ * cudaMalloc).  It runs the Chebyshev recurrence for exactly K steps on the
+ * caller's CSR (device pointers, int32 row_ptr and col_idx, natural order, the
+ * rules of gp_graph_create; not validated here) and writes n doubles to the
+ * device buffer y_out, on `stream` (cudaStream_t, NULL = default stream),
+ * stream-ordered.  Its scratch is one 16 MiB array in device memory that every
+ * GPU loading this library holds until the process exits, so n must be
+ * <= 1,048,576 (GP_EINVAL otherwise); 1 <= K <= 256; t <= 1000.  All calls on a
+ * device share that array: calls that overlap on the GPU race and corrupt each
+ * other.  The first call on a device looks up the array's address and should
+ * come before any stream capture.
+ */
+gp_status gp_query_static(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                          int32_t function, int32_t source, double param, int32_t K, double* y_out,
+                          void* stream);
+
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t gp_launch_count(void);
 
