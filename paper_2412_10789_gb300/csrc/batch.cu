@@ -1,13 +1,848 @@
-// Batched multi-source ChebyPower (gp_batch).
-#include "gp_internal.h"
+// Batched multi-source ChebyPower (gp_batch) and the column engine the
+// serving loop (serve.cpp) runs on.
+//
+// B queries are the columns of row-major blocks over the relabelled active
+// rows: Q_k, Q_{k-1} (storage FP32, BF16 or FP16) and y (FP32), n_active x B.
+// One fused SpMM pass advances every active column by one Chebyshev step
+// (Eq. res-recurrence): for each row u and column j
+//     acc_j = sum_{v in N(u)} Q_k[v][j]            (FP32; one B-wide row gather per edge)
+//     r_j   = 2 acc_j - d_u Q_{k-1}[u][j]
+//     Q_{k+1}[u][j] = r_j / d_u, y[u][j] += c_j r_j, ||r_j||_1 partial.
+// Each edge gathers a whole B*s-byte row, so the block amortises the col_idx
+// stream over B columns and uses every byte of the sectors it reads.
+//
+// Columns are independent queries: each has its own function, coefficient
+// table, tail, tolerance, step k and stop state (per-column stop rule of
+// Theorem 1 read for l1, as in the single query).  A control kernel between
+// passes retires columns whose rule fired and sets the next coefficient of the
+// others; retired columns are skipped (their y is final).  A column admitted
+// at global pass g gets Q_1 in buffer g&1 and Q_0 in buffer (g+1)&1, so every
+// pass reads buffer g&1 and writes buffer (g+1)&1 for all columns.
+//
+// Storage.  BF16/FP16 storage follows a warm-up schedule (Lemma 5: a rounding
+// error made at step l reaches y weighted by sum_{k>=l} |c_k|): passes run in
+// FP32 while any column's tail is at least warmup_tail, then two transition
+// passes (FP32 -> 16-bit) and 16-bit from there on.  FP16 stores Q * 2^12 to
+// keep small values of Q = r/d above FP16's subnormal range.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "batch.h"
 
 namespace gp {
 
-void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos) {
-  (void)g; (void)count; (void)reqs; (void)infos;
-  throw Error{GP_ENOTSUP, "gp_batch is not available in this build"};
+namespace {
+
+constexpr float kF16Scale = 4096.0f;
+constexpr int kChunk = 1024;       // entries per chunk of a long row
+constexpr int kBatchThreads = 256;
+
+// ---- 8-column vectors of each storage type
+struct V8 {
+  float x[8];
+};
+
+template <typename T>
+struct Store;
+
+template <>
+struct Store<float> {
+  static constexpr int bytes = 4;
+  struct Raw {
+    float4 a, b;
+  };
+  __device__ static __forceinline__ Raw load_raw(const void* base, int64_t row, int B, int cg) {
+    const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(base) + row * B + cg * 8);
+    return Raw{__ldg(p), __ldg(p + 1)};
+  }
+  __device__ static __forceinline__ void add(const Raw& r, float acc[8]) {
+    acc[0] += r.a.x; acc[1] += r.a.y; acc[2] += r.a.z; acc[3] += r.a.w;
+    acc[4] += r.b.x; acc[5] += r.b.y; acc[6] += r.b.z; acc[7] += r.b.w;
+  }
+  __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
+    const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(base) + row * B + cg * 8);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    return V8{{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w}};
+  }
+  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+    float4* p = reinterpret_cast<float4*>(static_cast<float*>(base) + row * B + cg * 8);
+    p[0] = make_float4(v.x[0], v.x[1], v.x[2], v.x[3]);
+    p[1] = make_float4(v.x[4], v.x[5], v.x[6], v.x[7]);
+  }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+  static constexpr int bytes = 2;
+  using Raw = uint4;
+  __device__ static __forceinline__ Raw load_raw(const void* base, int64_t row, int B, int cg) {
+    return __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * B + cg * 8));
+  }
+  __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      acc[2 * i] += __uint_as_float(u[i] << 16);
+      acc[2 * i + 1] += __uint_as_float(u[i] & 0xffff0000u);
+    }
+  }
+  __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * B + cg * 8));
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+    V8 v;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      v.x[2 * i] = __uint_as_float(u[i] << 16);
+      v.x[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+    }
+    return v;
+  }
+  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+    uint32_t u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x[2 * i], v.x[2 * i + 1]);
+      u[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(base) + row * B + cg * 8) = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+};
+
+template <>
+struct Store<__half> {
+  static constexpr int bytes = 2;
+  using Raw = uint4;
+  __device__ static __forceinline__ Raw load_raw(const void* base, int64_t row, int B, int cg) {
+    return __ldg(reinterpret_cast<const uint4*>(static_cast<const __half*>(base) + row * B + cg * 8));
+  }
+  __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[i]));
+      acc[2 * i] += f.x * (1.0f / kF16Scale);
+      acc[2 * i + 1] += f.y * (1.0f / kF16Scale);
+    }
+  }
+  __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(static_cast<const __half*>(base) + row * B + cg * 8));
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+    V8 v;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[i]));
+      v.x[2 * i] = f.x * (1.0f / kF16Scale);
+      v.x[2 * i + 1] = f.y * (1.0f / kF16Scale);
+    }
+    return v;
+  }
+  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+    uint32_t u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __half2 h = __floats2half2_rn(v.x[2 * i] * kF16Scale, v.x[2 * i + 1] * kF16Scale);
+      u[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    *reinterpret_cast<uint4*>(static_cast<__half*>(base) + row * B + cg * 8) = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+};
+
+struct SpmmArgs {
+  const int2* units;   // {row, chunk index or -1}
+  int64_t nunits;
+  const void* rp;
+  const int32_t* ci;
+  const void* qcur;    // Q_k  (gather type)
+  const void* qprev;   // Q_{k-1} (prev type)
+  void* qnext;         // Q_{k+1} (out type); equals qprev when the types match
+  float* y;            // n_active x B
+  const ColState* col; // per column: active flag and coefficient of this pass
+  float* norm;         // per column ||r_{k+1}||_1 of this pass
+  const int* poff;     // long rows: first chunk slot
+  float* part;         // long rows: chunk partial sums, [slot][B]
+  int* cnt;            // long rows: chunks finished
+  int64_t na;          // rows of the blocks (nodes with degree >= 1)
+  int B;
+};
+
+// Sum over neighbours of row `row` in [lo, hi): this lane accumulates its 8
+// columns (group cg) over the entries of its entry group g.
+template <typename TG, typename RP>
+__device__ __forceinline__ void gather_rows(const SpmmArgs& a, int64_t lo, int64_t hi, int g, int EG, int cg,
+                                            float acc[8]) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e0 = lo; e0 < hi; e0 += 32) {
+    const int ne = (int)min((int64_t)32, hi - e0);
+    const int myidx = lane < ne ? __ldcs(a.ci + e0 + lane) : 0;
+    // The loop is uniform across the warp (every lane reaches each shuffle);
+    // lane (g, cg) takes entries j0 + g + u*EG.
+    for (int j0 = 0; j0 < ne; j0 += 4 * EG) {
+      int v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __shfl_sync(0xffffffffu, myidx, min(j0 + g + u * EG, 31));
+      typename Store<TG>::Raw x[4];
+      // (a neighbour beyond the active rows can only come from an unvalidated,
+      // asymmetric CSR; its Q is zero and it is skipped)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + g + u * EG < ne && v[u] < a.na) x[u] = Store<TG>::load_raw(a.qcur, v[u], a.B, cg);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + g + u * EG < ne && v[u] < a.na) Store<TG>::add(x[u], acc);
+    }
+  }
 }
 
-void free_batch_work(Graph& g) { (void)g; }
+// Combine the entry groups' partial sums (lanes cg, cg + CG, cg + 2 CG, ...).
+__device__ __forceinline__ void reduce_groups(float acc[8], int CG) {
+  for (int off = CG; off < 32; off <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+  }
+}
+
+template <typename TP, typename TO>
+__device__ __forceinline__ void update_row(const SpmmArgs& a, const ColState* s_col, int64_t u, float d, int cg,
+                                           const float acc[8], float nrm[8]) {
+  const V8 prev = Store<TP>::load(a.qprev, u, a.B, cg);
+  float* yrow = a.y + u * a.B + cg * 8;
+  float4 y0 = *reinterpret_cast<const float4*>(yrow), y1 = *reinterpret_cast<const float4*>(yrow + 4);
+  float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+  V8 out = prev;
+  const float inv = 1.0f / d;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const ColState& cs = s_col[cg * 8 + i];
+    if (cs.active) {
+      const float r = 2.0f * acc[i] - d * prev.x[i];
+      out.x[i] = r * inv;
+      yv[i] = fmaf(cs.coef, r, yv[i]);
+      nrm[i] += fabsf(r);
+    }
+  }
+  Store<TO>::store(a.qnext, u, a.B, cg, out);
+  *reinterpret_cast<float4*>(yrow) = make_float4(yv[0], yv[1], yv[2], yv[3]);
+  *reinterpret_cast<float4*>(yrow + 4) = make_float4(yv[4], yv[5], yv[6], yv[7]);
+}
+
+template <typename RP, typename TG, typename TP, typename TO>
+__global__ void __launch_bounds__(kBatchThreads, 3) spmm_step_kernel(const __grid_constant__ SpmmArgs a) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  ColState* s_col = reinterpret_cast<ColState*>(s_raw);
+  float* s_norm = reinterpret_cast<float*>(s_raw + sizeof(ColState) * a.B);
+  for (int j = threadIdx.x; j < a.B; j += blockDim.x) {
+    s_col[j] = a.col[j];
+    s_norm[j] = 0.f;
+  }
+  __syncthreads();
+  const RP* rp = (const RP*)a.rp;
+  const int lane = threadIdx.x & 31;
+  const int CG = a.B / 8, EG = 32 / CG;
+  const int cg = lane % CG, g = lane / CG;
+  float nrm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < a.nunits; w += nwarps) {
+    const int2 unit = a.units[w];
+    const int64_t row = unit.x;
+    const int64_t beg = rp[row], end = rp[row + 1];
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (unit.y < 0) {
+      gather_rows<TG, RP>(a, beg, end, g, EG, cg, acc);
+      reduce_groups(acc, CG);
+      if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, acc, nrm);
+    } else {
+      const int p = unit.y;
+      const int64_t lo = beg + (int64_t)p * kChunk, hi = min(lo + (int64_t)kChunk, end);
+      gather_rows<TG, RP>(a, lo, hi, g, EG, cg, acc);
+      reduce_groups(acc, CG);
+      const int slot0 = a.poff[row], np = a.poff[row + 1] - slot0;
+      if (g == 0) {
+        float* dst = a.part + (int64_t)(slot0 + p) * a.B + cg * 8;
+        *reinterpret_cast<float4*>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      }
+      __threadfence();
+      __syncwarp();
+      int old = 0;
+      if (lane == 0) old = atomicAdd(&a.cnt[row], 1);
+      old = __shfl_sync(0xffffffffu, old, 0);
+      if (old == np - 1) {
+        // last chunk of the row: add the partials in chunk order, then update
+        __threadfence();
+        float tot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int i = g; i < np; i += EG) {
+          const float* src = a.part + (int64_t)(slot0 + i) * a.B + cg * 8;
+          const float4 p0 = __ldcg(reinterpret_cast<const float4*>(src));
+          const float4 p1 = __ldcg(reinterpret_cast<const float4*>(src + 4));
+          tot[0] += p0.x; tot[1] += p0.y; tot[2] += p0.z; tot[3] += p0.w;
+          tot[4] += p1.x; tot[5] += p1.y; tot[6] += p1.z; tot[7] += p1.w;
+        }
+        reduce_groups(tot, CG);
+        if (lane == 0) a.cnt[row] = 0;
+        if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, tot, nrm);
+      }
+    }
+  }
+  if (g == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (nrm[i] != 0.f) atomicAdd(&s_norm[cg * 8 + i], nrm[i]);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < a.B; j += blockDim.x)
+    if (s_norm[j] != 0.f) atomicAdd(&a.norm[j], s_norm[j]);
+}
+
+// Before each pass: fold the last pass's norm into each active column's
+// running max, apply its stop rule, and set the coefficient of the next step.
+__global__ void control_kernel(ColState* col, const ColParam* par, ColStat* stat, float* norm, int B, int kcap) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B) return;
+  ColState& cs = col[j];
+  const ColParam& p = par[j];
+  ColStat& st = stat[j];
+  if (!cs.active) {
+    norm[j] = 0.f;
+    return;
+  }
+  if (st.k > 1) st.C = fmaxf(st.C, norm[j]);  // ||r_k||_1 from the last pass
+  norm[j] = 0.f;
+  const bool stop_rule = p.tol >= 0.f && p.tail[st.k] * st.C <= p.tol;
+  const bool stop_fixed = p.kstop > 0 && st.k >= p.kstop;
+  if (stop_rule || stop_fixed || st.k >= kcap) {
+    cs.active = 0;
+    st.K = st.k;
+    st.done = 1;
+    return;
+  }
+  cs.coef = p.c[st.k + 1];
+  st.k += 1;
+}
+
+// Zero the given columns of Q_a, Q_b (and the 16-bit pair) and y over all rows.
+template <typename T>
+__device__ __forceinline__ void zero_col(void* base, int64_t row, int B, int j) {
+  static_cast<T*>(base)[row * B + j] = T(0.0f);
+}
+
+__global__ void reset_columns_kernel(int64_t na, int B, const int* cols, int ncols, float* fa, float* fb, void* ha,
+                                     void* hb, int h_is_bf16, float* y) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < na; r += (int64_t)gridDim.x * blockDim.x) {
+    for (int t = 0; t < ncols; ++t) {
+      const int j = cols[t];
+      fa[r * B + j] = 0.f;
+      fb[r * B + j] = 0.f;
+      y[r * B + j] = 0.f;
+      if (ha) {
+        if (h_is_bf16) {
+          zero_col<__nv_bfloat16>(ha, r, B, j);
+          zero_col<__nv_bfloat16>(hb, r, B, j);
+        } else {
+          zero_col<__half>(ha, r, B, j);
+          zero_col<__half>(hb, r, B, j);
+        }
+      }
+    }
+  }
+}
+
+// r_0 = e_s, r_1 = P e_s for column j (FP32 buffers): Q_0 -> q0, Q_1 -> q1,
+// y = c_0 r_0 + c_1 r_1.  One block per new column.
+template <typename RP>
+__global__ void init_columns_kernel(const void* rpv, const int32_t* ci, int64_t na, int B, const int* cols,
+                                    const int64_t* src,
+                                    const float* c0, const float* c1, float* q0, float* q1, float* y) {
+  const RP* rp = (const RP*)rpv;
+  const int j = cols[blockIdx.x];
+  const int64_t s = src[blockIdx.x];
+  const int64_t beg = rp[s], end = rp[s + 1];
+  const float ds = (float)(end - beg);
+  if (threadIdx.x == 0) {
+    q0[s * B + j] = 1.0f / ds;
+    y[s * B + j] = c0[blockIdx.x];
+  }
+  for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int32_t v = ci[e];
+    if (v >= na) continue;  // only an unvalidated asymmetric CSR lists an isolated row
+    const float dv = (float)(rp[v + 1] - rp[v]);
+    q1[(int64_t)v * B + j] = (float)(1.0 / ((double)ds * (double)dv));
+    y[(int64_t)v * B + j] = c1[blockIdx.x] / ds;
+  }
+}
+
+// y columns (relabelled rows) -> caller order, for the columns listed.  A CTA
+// takes 32 caller rows: it copies their 32 y rows (B floats each, contiguous)
+// into shared memory, then writes each listed column's 32 values coalesced.
+template <typename OUT>
+__global__ void output_columns_kernel(int64_t n, int64_t na, const int32_t* newid, const float* y, int B,
+                                      const int* cols, int ncols, OUT* const* outs) {
+  extern __shared__ __align__(16) float s_tile[];  // 32 x B
+  __shared__ int64_t s_row[32];
+  for (int64_t u0 = (int64_t)blockIdx.x * 32; u0 < n; u0 += (int64_t)gridDim.x * 32) {
+    if (threadIdx.x < 32) {
+      const int64_t u = u0 + threadIdx.x;
+      s_row[threadIdx.x] = u < n ? (int64_t)newid[u] : -1;
+    }
+    __syncthreads();
+    const int nvec = 32 * (B / 4);
+    for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+      const int r = v / (B / 4), c4 = v % (B / 4);
+      const int64_t i = s_row[r];
+      const float4 val = (i >= 0 && i < na) ? *reinterpret_cast<const float4*>(y + i * B + 4 * c4)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(s_tile + r * B + 4 * c4) = val;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t u = u0 + lane;
+    for (int t = warp; t < ncols; t += nw)
+      if (u < n) outs[t][u] = (OUT)s_tile[lane * B + cols[t]];
+    __syncthreads();
+  }
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+template <typename RP, typename TG, typename TP, typename TO>
+void launch_spmm(const SpmmArgs& a, cudaStream_t st) {
+  const size_t smem = (sizeof(ColState) + sizeof(float)) * a.B;
+  const int grid = device_sms() * (2048 / kBatchThreads);
+  spmm_step_kernel<RP, TG, TP, TO><<<grid, kBatchThreads, smem, st>>>(a);
+  GP_LAUNCHED();
+}
+
+template <typename RP, typename H>
+void launch_stage(const SpmmArgs& a, int stage, cudaStream_t st) {
+  switch (stage) {
+    case 0: launch_spmm<RP, float, float, float>(a, st); break;  // FP32
+    case 1: launch_spmm<RP, float, float, H>(a, st); break;      // first 16-bit write
+    case 2: launch_spmm<RP, H, float, H>(a, st); break;          // first 16-bit gather
+    default: launch_spmm<RP, H, H, H>(a, st); break;             // 16-bit
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ engine
+
+ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st)
+    : g_(g), B_(B), storage_(storage), st_(st) {
+  if (B < 8 || B > 256 || (B & (B - 1)))
+    throw Error{GP_EINVAL, "block width must be a power of two in [8, 256]"};
+  if (storage != GP_F32 && storage != GP_BF16 && storage != GP_F16)
+    throw Error{GP_EINVAL, "storage must be GP_F32, GP_BF16 or GP_F16"};
+  kcap_ = std::min(g.cfg.k_max, kMaxColK - 2);
+  const int64_t na = std::max<int64_t>(g.n_active, 1);
+  Allocator& A = g.alloc;
+  try {
+    f_[0] = (float*)A.get(sizeof(float) * na * B);
+    f_[1] = (float*)A.get(sizeof(float) * na * B);
+    if (storage != GP_F32) {
+      h_[0] = A.get(2 * na * B);
+      h_[1] = A.get(2 * na * B);
+    }
+    y_ = (float*)A.get(sizeof(float) * na * B);
+    col_ = (ColState*)A.get(sizeof(ColState) * B);
+    par_ = (ColParam*)A.get(sizeof(ColParam) * B);
+    stat_ = (ColStat*)A.get(sizeof(ColStat) * B);
+    norm_ = (float*)A.get(sizeof(float) * B);
+    scratch_ = (int*)A.get(sizeof(int) * 4 * B + sizeof(int64_t) * B + sizeof(float) * 2 * B + 16);
+    outs_ = A.get(sizeof(void*) * B);
+    // long-row chunk table for kChunk-entry chunks
+    const std::vector<int64_t>& rp = g.h_rp_relabelled;
+    std::vector<int2> units;
+    std::vector<int> poff(1, 0);
+    int64_t row = 0;
+    while (row < g.n_active && rp[row + 1] - rp[row] > kChunk) {
+      const int64_t np = (rp[row + 1] - rp[row] + kChunk - 1) / kChunk;
+      for (int64_t p = 0; p < np; ++p) units.push_back(make_int2((int)row, (int)p));
+      poff.push_back(poff.back() + (int)np);
+      ++row;
+    }
+    nlong_ = (int)row;
+    for (; row < g.n_active; ++row) units.push_back(make_int2((int)row, -1));
+    nunits_ = (int64_t)units.size();
+    units_ = (int2*)A.get(sizeof(int2) * std::max<size_t>(units.size(), 1));
+    poff_ = (int*)A.get(sizeof(int) * poff.size());
+    part_ = (float*)A.get(sizeof(float) * (size_t)std::max(poff.back(), 1) * B);
+    cnt_ = (int*)A.get(sizeof(int) * std::max(nlong_, 1));
+    if (!units.empty())
+      GP_CUDA_TRY(cudaMemcpyAsync(units_, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, st_));
+    GP_CUDA_TRY(cudaMemcpyAsync(poff_, poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice, st_));
+    GP_CUDA_TRY(cudaMemsetAsync(cnt_, 0, sizeof(int) * std::max(nlong_, 1), st_));
+    GP_CUDA_TRY(cudaMemsetAsync(col_, 0, sizeof(ColState) * B, st_));
+    GP_CUDA_TRY(cudaMemsetAsync(par_, 0, sizeof(ColParam) * B, st_));
+    GP_CUDA_TRY(cudaMemsetAsync(stat_, 0, sizeof(ColStat) * B, st_));
+    GP_CUDA_TRY(cudaMemsetAsync(norm_, 0, sizeof(float) * B, st_));
+    GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  } catch (...) {
+    release();
+    throw;
+  }
+  slots_.assign(B, Slot{});
+}
+
+ColumnEngine::~ColumnEngine() { release(); }
+
+void ColumnEngine::release() {
+  if (st_) cudaStreamSynchronize(st_);
+  Allocator& A = g_.alloc;
+  for (void* p : {(void*)f_[0], (void*)f_[1], h_[0], h_[1], (void*)y_, (void*)col_, (void*)par_, (void*)stat_,
+                  (void*)norm_, (void*)scratch_, outs_, stage_, (void*)units_, (void*)poff_, (void*)part_,
+                  (void*)cnt_})
+    A.put(p);
+  stat_ = nullptr;
+  stage_ = nullptr;
+  f_[0] = f_[1] = nullptr;
+  h_[0] = h_[1] = nullptr;
+  y_ = nullptr;
+  col_ = nullptr;
+  par_ = nullptr;
+  norm_ = nullptr;
+  scratch_ = nullptr;
+  outs_ = nullptr;
+  units_ = nullptr;
+  poff_ = nullptr;
+  part_ = nullptr;
+  cnt_ = nullptr;
+}
+
+size_t ColumnEngine::bytes_per_column(const Graph& g, gp_dtype storage) {
+  const size_t na = (size_t)std::max<int64_t>(g.n_active, 1);
+  return na * (4 + 4 + 4 + (storage == GP_F32 ? 0 : 4));
+}
+
+int ColumnEngine::free_slots() const {
+  int f = 0;
+  for (const Slot& s : slots_) f += !s.busy;
+  return f;
+}
+
+// Admit requests into free slots.  Returns the slots used (one per request, -1
+// for an isolated source, which is answered at once).
+std::vector<int> ColumnEngine::admit(const std::vector<gp_request>& reqs, std::vector<uint64_t> tags) {
+  std::vector<int> slots(reqs.size(), -1);
+  std::vector<int> cols;
+  std::vector<int64_t> srcs;
+  std::vector<float> c0, c1;
+  std::vector<ColParam> params;
+  std::vector<int> tag_of_param;
+  const int kcap = kcap_;
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    const gp_request& r = reqs[i];
+    const int64_t deg = g_.h_deg[r.source];
+    if (deg == 0) {
+      // P e_s = 0: y = f(0) e_s, written directly (no slot)
+      const double f0 = r.function == GP_FN_PPR ? r.param : std::exp(-r.param);
+      write_point(r, f0);
+      continue;
+    }
+    int slot = -1;
+    for (int j = 0; j < B_; ++j)
+      if (!slots_[j].busy) {
+        slot = j;
+        break;
+      }
+    if (slot < 0) throw Error{GP_EBUSY, "no free column"};
+    slots_[slot].busy = true;
+    slots_[slot].req = r;
+    slots_[slot].tag = i < tags.size() ? tags[i] : 0;
+    slots_[slot].t_admit = std::chrono::steady_clock::now();
+    slots[i] = slot;
+    std::vector<double> c, tail;
+    cheb_coefficients(r.function, r.param, kcap, c, tail);
+    ColParam p;
+    std::memset(&p, 0, sizeof(p));
+    slots_[slot].tails.assign(tail.begin(), tail.end());
+    slots_[slot].tails.resize(kMaxColK, 0.0);
+    for (int k = 0; k <= kcap && k < kMaxColK; ++k) {
+      p.c[k] = (float)c[k];
+      p.tail[k] = (float)tail[k];
+    }
+    p.tol = r.k_rule == GP_K_TAIL ? (float)r.l1_tol : -1.0f;
+    p.kstop = r.k_rule == GP_K_FIXED ? r.k_fixed
+              : r.k_rule == GP_K_PAPER ? std::min(kcap - 1, paper_k(r.function, r.param, r.l1_tol))
+                                       : 0;
+    p.warm = 0;
+    for (int k = 0; k <= kcap && k < kMaxColK; ++k)
+      if (tail[k] < g_.cfg.warmup_tail) {
+        p.warm = k;
+        break;
+      }
+    params.push_back(p);
+    cols.push_back(slot);
+    srcs.push_back(g_.h_newid[r.source]);
+    c0.push_back((float)c[0]);
+    c1.push_back((float)c[1]);
+  }
+  if (cols.empty()) return slots;
+  const int nc = (int)cols.size();
+  // upload parameters and init state of the new columns
+  int* d_cols = scratch_;
+  int64_t* d_src = reinterpret_cast<int64_t*>(scratch_ + 4 * B_);
+  float* d_c0 = reinterpret_cast<float*>(d_src + B_);
+  float* d_c1 = d_c0 + B_;
+  GP_CUDA_TRY(cudaMemcpyAsync(d_cols, cols.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(d_src, srcs.data(), sizeof(int64_t) * nc, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(d_c0, c0.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(d_c1, c1.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, st_));
+  const ColState cs_on{1, 0.f};
+  const ColStat st0{1, 0, 0, 1.0f};  // r_0, r_1 set by the init; ||r_0||_1 = ||r_1||_1 = 1
+  for (int t = 0; t < nc; ++t) {
+    GP_CUDA_TRY(cudaMemcpyAsync(par_ + cols[t], &params[t], sizeof(ColParam), cudaMemcpyHostToDevice, st_));
+    GP_CUDA_TRY(cudaMemcpyAsync(col_ + cols[t], &cs_on, sizeof(ColState), cudaMemcpyHostToDevice, st_));
+    GP_CUDA_TRY(cudaMemcpyAsync(stat_ + cols[t], &st0, sizeof(ColStat), cudaMemcpyHostToDevice, st_));
+  }
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));  // host vectors above are pageable and local
+  const int sms = device_sms();
+  reset_columns_kernel<<<sms * 4, 256, 0, st_>>>(g_.n_active, B_, d_cols, nc, f_[0], f_[1], h_[0], h_[1],
+                                                  storage_ == GP_BF16 ? 1 : 0, y_);
+  GP_LAUNCHED();
+  // Q_1 goes to the buffer the next pass gathers (pass_ & 1), Q_0 to the other.
+  float* q1 = f_[pass_ & 1];
+  float* q0 = f_[(pass_ + 1) & 1];
+  if (g_.rp64)
+    init_columns_kernel<int64_t><<<nc, 256, 0, st_>>>(g_.rp, g_.ci, g_.n_active, B_, d_cols, d_src, d_c0, d_c1, q0, q1, y_);
+  else
+    init_columns_kernel<int32_t><<<nc, 256, 0, st_>>>(g_.rp, g_.ci, g_.n_active, B_, d_cols, d_src, d_c0, d_c1, q0, q1, y_);
+  GP_LAUNCHED();
+  active_ += nc;
+  for (const ColParam& p : params) warm_ = std::max(warm_, p.warm);
+  return slots;
+}
+
+// One fused pass over all active columns (control kernel + SpMM step).
+void ColumnEngine::pass() {
+  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_);
+  GP_LAUNCHED();
+  // storage stage of this pass: FP32 until every column's warm-up has passed
+  int stage = 0;
+  if (storage_ != GP_F32) {
+    if (h_pass_ < 0 && pass_16_ok()) h_pass_ = pass_;
+    if (h_pass_ >= 0) stage = std::min(3, pass_ - h_pass_ + 1);
+  }
+  SpmmArgs a;
+  a.units = units_;
+  a.nunits = nunits_;
+  a.rp = g_.rp;
+  a.ci = g_.ci;
+  const int cur = pass_ & 1, nxt = (pass_ + 1) & 1;
+  a.qcur = stage >= 2 ? h_[cur] : (const void*)f_[cur];
+  a.qprev = stage >= 3 ? h_[nxt] : (const void*)f_[nxt];
+  a.qnext = stage >= 1 ? h_[nxt] : (void*)f_[nxt];
+  a.y = y_;
+  a.col = col_;
+  a.norm = norm_;
+  a.poff = poff_;
+  a.part = part_;
+  a.cnt = cnt_;
+  a.na = g_.n_active;
+  a.B = B_;
+  if (g_.rp64) {
+    if (storage_ == GP_F16) launch_stage<int64_t, __half>(a, stage, st_);
+    else launch_stage<int64_t, __nv_bfloat16>(a, stage, st_);
+  } else {
+    if (storage_ == GP_F16) launch_stage<int32_t, __half>(a, stage, st_);
+    else launch_stage<int32_t, __nv_bfloat16>(a, stage, st_);
+  }
+  ++pass_;
+  ++passes_total_;
+}
+
+// The 16-bit phase may start once every column present has passed its
+// warm-up steps (columns admitted later would have to warm up in 16 bits, so
+// 16-bit storage is used only by engines that admit all columns at once).
+bool ColumnEngine::pass_16_ok() const { return pass_ >= warm_; }
+
+// Columns whose stop rule has fired: read their state, write their outputs,
+// and free their slots.  Returns the finished slots.
+std::vector<ColumnEngine::Finished> ColumnEngine::collect(bool force_all) {
+  std::vector<Finished> fin;
+  std::vector<ColStat> stat(B_);
+  GP_CUDA_TRY(cudaMemcpyAsync(stat.data(), stat_, sizeof(ColStat) * B_, cudaMemcpyDeviceToHost, st_));
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  std::vector<int> cols;
+  for (int j = 0; j < B_; ++j)
+    if (slots_[j].busy && (stat[j].done || force_all)) cols.push_back(j);
+  if (cols.empty()) return fin;
+  write_outputs(cols);
+  for (int j : cols) {
+    Finished f;
+    f.slot = j;
+    f.tag = slots_[j].tag;
+    f.req = slots_[j].req;
+    f.K = stat[j].done ? stat[j].K : stat[j].k;
+    f.C = stat[j].C;
+    f.tail_bound = (double)slots_[j].tails[std::min(f.K, kMaxColK - 1)] * stat[j].C;
+    f.t_admit = slots_[j].t_admit;
+    f.k16_from = h_pass_ >= 0 ? h_pass_ : f.K + 1;
+    fin.push_back(f);
+    slots_[j].busy = false;
+    const ColStat zero{0, 0, 0, 0.f};
+    GP_CUDA_TRY(cudaMemcpyAsync(stat_ + j, &zero, sizeof(ColStat), cudaMemcpyHostToDevice, st_));
+    ColState cs{0, 0.f};
+    GP_CUDA_TRY(cudaMemcpyAsync(col_ + j, &cs, sizeof(ColState), cudaMemcpyHostToDevice, st_));
+    --active_;
+  }
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  return fin;
+}
+
+void ColumnEngine::write_outputs(const std::vector<int>& cols) {
+  // one launch per output type and location; host outputs go through staging
+  std::vector<int> dcol64, dcol32;
+  std::vector<void*> p64, p32;
+  std::vector<std::pair<int, void*>> host;
+  for (int j : cols) {
+    const gp_request& r = slots_[j].req;
+    if (!r.y_on_device) {
+      host.push_back({j, r.y_out});
+      continue;
+    }
+    if (r.out_dtype == GP_F64) {
+      dcol64.push_back(j);
+      p64.push_back(r.y_out);
+    } else {
+      dcol32.push_back(j);
+      p32.push_back(r.y_out);
+    }
+  }
+  auto launch = [&](const std::vector<int>& cl, const std::vector<void*>& ptrs, bool f64) {
+    if (cl.empty()) return;
+    int* d_cols = scratch_ + 2 * B_;
+    GP_CUDA_TRY(cudaMemcpyAsync(d_cols, cl.data(), sizeof(int) * cl.size(), cudaMemcpyHostToDevice, st_));
+    GP_CUDA_TRY(cudaMemcpyAsync(outs_, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice, st_));
+    const int grid = device_sms() * 4;
+    const size_t smem = sizeof(float) * 32 * B_;
+    if (f64)
+      output_columns_kernel<double><<<grid, 256, smem, st_>>>(g_.n, g_.n_active, g_.newid, y_, B_, d_cols,
+                                                              (int)cl.size(), (double* const*)outs_);
+    else
+      output_columns_kernel<float><<<grid, 256, smem, st_>>>(g_.n, g_.n_active, g_.newid, y_, B_, d_cols,
+                                                             (int)cl.size(), (float* const*)outs_);
+    GP_LAUNCHED();
+    GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  };
+  launch(dcol64, p64, true);
+  launch(dcol32, p32, false);
+  if (!host.empty()) {
+    if (!stage_) stage_ = g_.alloc.get(sizeof(double) * g_.n);
+    for (auto& h : host) {
+      const gp_request& r = slots_[h.first].req;
+      std::vector<int> one{h.first};
+      std::vector<void*> ptr{stage_};
+      launch(one, ptr, r.out_dtype == GP_F64);
+      const size_t esz = r.out_dtype == GP_F64 ? 8 : 4;
+      GP_CUDA_TRY(cudaMemcpyAsync(h.second, stage_, esz * g_.n, cudaMemcpyDeviceToHost, st_));
+      GP_CUDA_TRY(cudaStreamSynchronize(st_));
+    }
+  }
+}
+
+void ColumnEngine::write_point(const gp_request& r, double f0) {
+  const size_t esz = r.out_dtype == GP_F64 ? 8 : 4;
+  std::vector<unsigned char> host(esz * g_.n, 0);
+  if (r.out_dtype == GP_F64)
+    reinterpret_cast<double*>(host.data())[r.source] = f0;
+  else
+    reinterpret_cast<float*>(host.data())[r.source] = (float)f0;
+  GP_CUDA_TRY(cudaMemcpyAsync(r.y_out, host.data(), host.size(),
+                              r.y_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st_));
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));
+}
+
+// ------------------------------------------------------------------ gp_batch
+
+void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos) {
+  for (int i = 0; i < count; ++i) {
+    const gp_request& r = reqs[i];
+    GP_REQUIRE(r.function == GP_FN_PPR || r.function == GP_FN_HKPR, "function must be GP_FN_PPR or GP_FN_HKPR");
+    GP_REQUIRE(r.source >= 0 && (int64_t)r.source < g.n, "source out of range");
+    if (r.function == GP_FN_PPR)
+      GP_REQUIRE(r.param > 0.0 && r.param < 1.0, "alpha must be in (0, 1)");
+    else
+      GP_REQUIRE(r.param > 0.0 && r.param <= 1e4, "t must be in (0, 1e4]");
+    GP_REQUIRE(r.l1_tol > 0.0 && r.l1_tol < 1.0, "l1_tol must be in (0, 1)");
+    GP_REQUIRE(r.out_dtype == GP_F64 || r.out_dtype == GP_F32, "out_dtype must be GP_F64 or GP_F32");
+    GP_REQUIRE(r.y_out != nullptr, "y_out is NULL");
+    GP_REQUIRE(r.k_rule == GP_K_TAIL || r.k_rule == GP_K_PAPER || r.k_rule == GP_K_FIXED, "bad k_rule");
+    if (r.k_rule == GP_K_FIXED)
+      GP_REQUIRE(r.k_fixed >= 1 && r.k_fixed < g.cfg.k_max, "k_fixed must be in [1, k_max)");
+  }
+  if (count == 0) return;
+  const int B = g.cfg.block_width > 0 ? g.cfg.block_width : std::min(256, std::max(8, (int)(1u << (32 - __builtin_clz((unsigned)std::max(count, 8) - 1)))));
+  BatchCache* bc = static_cast<BatchCache*>(g.batch);
+  if (!bc) {
+    bc = new BatchCache();
+    g.batch = bc;
+  }
+  if (!bc->eng || bc->B != B || bc->storage != g.cfg.storage) {
+    bc->eng.reset();
+    bc->eng.reset(new ColumnEngine(g, B, g.cfg.storage, g.stream));
+    bc->B = B;
+    bc->storage = g.cfg.storage;
+  }
+  ColumnEngine& eng = *bc->eng;
+  eng.restart();
+  auto t0 = std::chrono::steady_clock::now();
+  for (int base = 0; base < count; base += B) {
+    const int nb = std::min(B, count - base);
+    std::vector<gp_request> block(reqs + base, reqs + base + nb);
+    std::vector<uint64_t> tags(nb);
+    for (int i = 0; i < nb; ++i) tags[i] = (uint64_t)(base + i);
+    eng.restart();
+    eng.admit(block, tags);
+    // isolated sources were answered at admission
+    for (int i = 0; i < nb; ++i)
+      if (infos && g.h_deg[reqs[base + i].source] == 0) {
+        infos[base + i].K = 0;
+        infos[base + i].k16_from = 1;
+        infos[base + i].tail_bound = 0.0;
+        infos[base + i].max_r_l1 = 1.0;
+        infos[base + i].ms = 0.0;
+      }
+    int since_check = 0;
+    while (eng.active() > 0) {
+      eng.pass();
+      if (++since_check >= 4) {
+        since_check = 0;
+        for (const auto& f : eng.collect(false)) {
+          if (infos) {
+            gp_query_info& in = infos[f.tag];
+            in.K = f.K;
+            in.k16_from = f.k16_from;
+            in.tail_bound = f.tail_bound;
+            in.max_r_l1 = f.C;
+            in.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+          }
+        }
+      }
+    }
+  }
+}
+
+void free_batch_work(Graph& g) {
+  BatchCache* bc = static_cast<BatchCache*>(g.batch);
+  delete bc;
+  g.batch = nullptr;
+}
+
+void ColumnEngine::restart() {
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  pass_ = 0;
+  h_pass_ = -1;
+  warm_ = 0;
+}
 
 }  // namespace gp

@@ -1,0 +1,125 @@
+// Column engine: B queries as the columns of row-major blocks, advanced
+// together by one fused SpMM pass (batch.cu).  Used by gp_batch and by the
+// serving loop.
+#pragma once
+
+#include <chrono>
+#include <memory>
+#include <vector>
+
+#include "gp_internal.h"
+
+namespace gp {
+
+constexpr int kMaxColK = 128;  // coefficient table length per column (K <= kMaxColK - 2)
+
+// Per-column values the step kernel reads each pass.
+struct ColState {
+  int active;
+  float coef;  // c_{k+1} of this pass
+};
+
+// Per-column constants, written at admission.
+struct ColParam {
+  float c[kMaxColK];     // Chebyshev coefficients c_0..
+  float tail[kMaxColK];  // tail(k) = sum_{l>k} |c_l|
+  float tol;             // l1 tolerance of the stop rule (< 0: no rule)
+  int kstop;             // fixed K (> 0) or 0
+  int warm;              // first k with tail(k) < warmup_tail
+  int pad;
+};
+
+// Per-column progress, updated by the control kernel.
+struct ColStat {
+  int k;      // r_k is the newest term in y
+  int K;      // final K once done
+  int done;   // the stop rule (or the fixed K) fired
+  float C;    // max_{l<=k} ||r_l||_1
+};
+
+class ColumnEngine {
+ public:
+  struct Finished {
+    int slot;
+    uint64_t tag;
+    gp_request req;
+    int K;
+    int k16_from;
+    float C;
+    double tail_bound;
+    std::chrono::steady_clock::time_point t_admit;
+  };
+
+  ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st);
+  ~ColumnEngine();
+  ColumnEngine(const ColumnEngine&) = delete;
+  ColumnEngine& operator=(const ColumnEngine&) = delete;
+
+  // Device bytes one column occupies (Q pair, 16-bit pair, y).
+  static size_t bytes_per_column(const Graph& g, gp_dtype storage);
+
+  int width() const { return B_; }
+  int active() const { return active_; }
+  int free_slots() const;
+  uint64_t passes() const { return passes_total_; }
+  // Put requests into free columns (isolated sources are answered at once and
+  // take no column).  Returns the column of each request (-1: answered).
+  std::vector<int> admit(const std::vector<gp_request>& reqs, std::vector<uint64_t> tags);
+  // One fused pass: stop rule and coefficients, then the SpMM step.
+  void pass();
+  // Write the outputs of the columns whose rule fired (all busy columns when
+  // force_all), free them, and report them.
+  std::vector<Finished> collect(bool force_all);
+  // Forget the pass count and the 16-bit schedule (no column may be busy).
+  void restart();
+
+ private:
+  void release();
+  bool pass_16_ok() const;
+  void write_outputs(const std::vector<int>& cols);
+  void write_point(const gp_request& r, double f0);
+
+  struct Slot {
+    bool busy = false;
+    gp_request req{};
+    uint64_t tag = 0;
+    std::chrono::steady_clock::time_point t_admit;
+    std::vector<double> tails;  // FP64 tail(k) for the report
+  };
+
+  Graph& g_;
+  int B_;
+  gp_dtype storage_;
+  cudaStream_t st_;
+  int kcap_ = 0;
+  float* f_[2] = {nullptr, nullptr};  // FP32 Q pair
+  void* h_[2] = {nullptr, nullptr};   // 16-bit Q pair
+  float* y_ = nullptr;
+  ColState* col_ = nullptr;
+  ColParam* par_ = nullptr;
+  ColStat* stat_ = nullptr;
+  float* norm_ = nullptr;
+  int* scratch_ = nullptr;
+  void* outs_ = nullptr;
+  void* stage_ = nullptr;
+  int2* units_ = nullptr;
+  int64_t nunits_ = 0;
+  int nlong_ = 0;
+  int* poff_ = nullptr;
+  float* part_ = nullptr;
+  int* cnt_ = nullptr;
+  std::vector<Slot> slots_;
+  int active_ = 0;
+  int pass_ = 0;
+  int h_pass_ = -1;
+  int warm_ = 0;
+  uint64_t passes_total_ = 0;
+};
+
+struct BatchCache {
+  std::unique_ptr<ColumnEngine> eng;
+  int B = 0;
+  gp_dtype storage = GP_F32;
+};
+
+}  // namespace gp

@@ -145,6 +145,7 @@ struct Graph {
   int32_t* newid = nullptr;   // newid[u] = relabelled id of caller node u, device
   std::vector<int32_t> h_newid;  // host copy of newid
   std::vector<int32_t> h_deg;    // host copy of the (caller-order) degrees
+  std::vector<int64_t> h_rp_relabelled;  // host copy of the relabelled row offsets
   Schedule sched;
   gp_config cfg{};
   Allocator alloc;

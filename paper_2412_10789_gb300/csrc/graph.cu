@@ -249,6 +249,7 @@ void ingest(Graph& g, const void* row_ptr_in, int in_rp64, const int32_t* col_id
   g.h_newid.swap(newid);
   g.h_deg.swap(deg);
   build_schedule(g, nrp);
+  g.h_rp_relabelled.swap(nrp);
 }
 
 void destroy_graph(Graph* g) {

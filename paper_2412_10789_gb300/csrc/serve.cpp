@@ -1,22 +1,249 @@
-// Continuous-batching service (gp_submit / gp_poll).
-#include "gp_internal.h"
+// Continuous-batching service (gp_submit / gp_poll / gp_serve_stats).
+//
+// One service thread per graph owns a column engine (batch.h) on its own
+// stream.  Its width (columns = query slots) is what the memory budget allows
+// (cfg.mem_budget, default 80% of the free device memory, at
+// ColumnEngine::bytes_per_column each, capped by cfg.block_width or 256), so a
+// free column is also free memory for one more query.  Each iteration admits
+// queued requests into free columns, runs one fused pass over all active
+// columns (the per-column stop rule runs on the device in the pass's control
+// kernel), and every few passes collects the retired columns: their y is
+// written to the request's y_out, the ticket completes, and the column is free
+// for the next request.  Requests therefore join and leave the running block
+// while the others keep going; their work shares every pass.
+#include <algorithm>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "batch.h"
 
 namespace gp {
 
+namespace {
+
+constexpr size_t kQueueCap = 1 << 20;
+constexpr int kCollectEvery = 2;
+
+struct Ticket {
+  uint64_t id;
+  gp_request req;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Done {
+  gp_status status;
+  gp_query_info info;
+};
+
+struct Serve {
+  Graph* g = nullptr;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::unique_ptr<ColumnEngine> eng;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Ticket> pending;
+  std::unordered_map<uint64_t, std::chrono::steady_clock::time_point> inflight;  // admitted
+  std::unordered_map<uint64_t, Done> done;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::string error;
+  std::thread th;
+  uint64_t completed = 0, passes = 0;
+  double active_sum = 0.0;
+
+  void run() {
+    cudaSetDevice(device);
+    try {
+      loop();
+    } catch (const Error& e) {
+      fail(e.status, e.msg);
+    } catch (const std::exception& e) {
+      fail(GP_EINVAL, e.what());
+    }
+  }
+
+  void fail(gp_status st, const std::string& msg) {
+    std::lock_guard<std::mutex> lk(mu);
+    error = msg;
+    Done d{st, {}};
+    for (auto& kv : inflight) done[kv.first] = d;
+    inflight.clear();
+    for (auto& t : pending) done[t.id] = d;
+    pending.clear();
+    stop = true;
+    cv.notify_all();
+  }
+
+  void loop() {
+    int since_collect = 0;
+    for (;;) {
+      std::vector<gp_request> reqs;
+      std::vector<uint64_t> tags;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return stop || !pending.empty() || eng->active() > 0; });
+        if (stop) return;
+        int free = eng->free_slots();
+        while (free > 0 && !pending.empty()) {
+          Ticket t = pending.front();
+          pending.pop_front();
+          reqs.push_back(t.req);
+          tags.push_back(t.id);
+          inflight[t.id] = t.t_submit;
+          --free;
+        }
+      }
+      if (!reqs.empty()) {
+        std::vector<int> slots = eng->admit(reqs, tags);
+        // isolated sources are answered at admission
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t i = 0; i < slots.size(); ++i)
+          if (slots[i] < 0) finish(tags[i], 0, 1.0, 0.0);
+      }
+      if (eng->active() > 0) {
+        eng->pass();
+        ++passes;
+        active_sum += eng->active();
+        if (++since_collect >= kCollectEvery) {
+          since_collect = 0;
+          auto fin = eng->collect(false);
+          std::lock_guard<std::mutex> lk(mu);
+          for (const auto& f : fin) finish(f.tag, f.K, f.C, f.tail_bound);
+        }
+      }
+    }
+  }
+
+  // mu held
+  void finish(uint64_t id, int K, double C, double bound) {
+    auto it = inflight.find(id);
+    Done d;
+    d.status = GP_OK;
+    std::memset(&d.info, 0, sizeof(d.info));
+    d.info.K = K;
+    d.info.k16_from = K + 1;
+    d.info.max_r_l1 = C;
+    d.info.tail_bound = bound;
+    if (it != inflight.end()) {
+      d.info.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - it->second).count();
+      inflight.erase(it);
+    }
+    done[id] = d;
+    ++completed;
+    cv.notify_all();
+  }
+};
+
+Serve* get_serve(Graph& g) {
+  std::lock_guard<std::recursive_mutex> lk(g.mu);
+  if (g.serve) return static_cast<Serve*>(g.serve);
+  std::unique_ptr<Serve> s(new Serve());
+  s->g = &g;
+  GP_CUDA_TRY(cudaGetDevice(&s->device));
+  GP_CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+  size_t free_b = 0, total_b = 0;
+  GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const size_t budget = g.cfg.mem_budget ? g.cfg.mem_budget : (size_t)(0.8 * (double)free_b);
+  const size_t per_col = ColumnEngine::bytes_per_column(g, GP_F32);
+  int cap = g.cfg.block_width > 0 ? g.cfg.block_width : 256;
+  int width = 8;
+  while (width * 2 <= cap && (size_t)(width * 2) * per_col <= budget) width *= 2;
+  if ((size_t)width * per_col > budget) throw Error{GP_ENOMEM, "memory budget is below eight query columns"};
+  // Columns join at different passes, so they cannot share one 16-bit
+  // switch-over: the service stores its blocks in FP32.
+  s->eng.reset(new ColumnEngine(g, width, GP_F32, s->stream));
+  s->th = std::thread([p = s.get()] { p->run(); });
+  g.serve = s.release();
+  return static_cast<Serve*>(g.serve);
+}
+
+void validate(const Graph& g, const gp_request& r) {
+  GP_REQUIRE(r.function == GP_FN_PPR || r.function == GP_FN_HKPR, "function must be GP_FN_PPR or GP_FN_HKPR");
+  GP_REQUIRE(r.source >= 0 && (int64_t)r.source < g.n, "source out of range");
+  if (r.function == GP_FN_PPR)
+    GP_REQUIRE(r.param > 0.0 && r.param < 1.0, "alpha must be in (0, 1)");
+  else
+    GP_REQUIRE(r.param > 0.0 && r.param <= 1e4, "t must be in (0, 1e4]");
+  GP_REQUIRE(r.l1_tol > 0.0 && r.l1_tol < 1.0, "l1_tol must be in (0, 1)");
+  GP_REQUIRE(r.out_dtype == GP_F64 || r.out_dtype == GP_F32, "out_dtype must be GP_F64 or GP_F32");
+  GP_REQUIRE(r.y_out != nullptr, "y_out is NULL");
+  GP_REQUIRE(r.k_rule == GP_K_TAIL || r.k_rule == GP_K_PAPER || r.k_rule == GP_K_FIXED, "bad k_rule");
+  if (r.k_rule == GP_K_FIXED) GP_REQUIRE(r.k_fixed >= 1 && r.k_fixed < g.cfg.k_max, "k_fixed must be in [1, k_max)");
+}
+
+}  // namespace
+
 uint64_t serve_submit(Graph& g, const gp_request& req) {
-  (void)g; (void)req;
-  throw Error{GP_ENOTSUP, "gp_submit is not available in this build"};
+  validate(g, req);
+  Serve* s = get_serve(g);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) throw Error{GP_ECUDA, "the service stopped: " + s->error};
+  if (s->pending.size() >= kQueueCap) throw Error{GP_EBUSY, "the request queue is full"};
+  const uint64_t id = s->next_ticket++;
+  s->pending.push_back(Ticket{id, req, std::chrono::steady_clock::now()});
+  s->cv.notify_all();
+  return id;
 }
+
 gp_status serve_poll(Graph& g, uint64_t ticket, gp_query_info* info) {
-  (void)g; (void)ticket; (void)info;
-  throw Error{GP_ENOTSUP, "gp_poll is not available in this build"};
+  Serve* s = static_cast<Serve*>(g.serve);
+  if (!s) {
+    set_last_error("unknown ticket");
+    return GP_ENOTFOUND;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->done.find(ticket);
+  if (it != s->done.end()) {
+    const Done d = it->second;
+    s->done.erase(it);
+    if (d.status != GP_OK) {
+      set_last_error(s->error);
+      return d.status;
+    }
+    if (info) *info = d.info;
+    return GP_OK;
+  }
+  if (s->inflight.count(ticket)) return GP_EAGAIN;
+  for (const Ticket& t : s->pending)
+    if (t.id == ticket) return GP_EAGAIN;
+  set_last_error("unknown ticket");
+  return GP_ENOTFOUND;
 }
+
 void serve_stats(Graph& g, uint64_t* completed, uint64_t* steps, double* mean_active) {
-  (void)g;
-  if (completed) *completed = 0;
-  if (steps) *steps = 0;
-  if (mean_active) *mean_active = 0.0;
+  Serve* s = static_cast<Serve*>(g.serve);
+  uint64_t c = 0, p = 0;
+  double m = 0.0;
+  if (s) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    c = s->completed;
+    p = s->passes;
+    m = p ? s->active_sum / (double)p : 0.0;
+  }
+  if (completed) *completed = c;
+  if (steps) *steps = p;
+  if (mean_active) *mean_active = m;
 }
-void serve_shutdown(Graph& g) { (void)g; }
+
+void serve_shutdown(Graph& g) {
+  Serve* s = static_cast<Serve*>(g.serve);
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  if (s->th.joinable()) s->th.join();
+  s->eng.reset();
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+  g.serve = nullptr;
+}
 
 }  // namespace gp

@@ -1,0 +1,188 @@
+"""GPU tests of the batched column engine (gp_batch) and the serving loop
+(gp_submit / gp_poll) against the FP64 oracle, through the C ABI.
+
+Batched columns accumulate the SpMM in plain FP32 and keep y in FP32 (the
+single query uses compensated sums and a float-pair y), so the fixed-K parity
+bar here is l1 <= 1e-6 and max-abs <= 1e-7: FP32 rounding of y values up to
+~0.4 is 2.4e-8 per operation, over ~30 steps.  With 16-bit storage the bar is
+the query's own l1 tolerance against the converged oracle vector.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+KINDS = {0: "ppr", 1: "hkpr"}
+MIX = [(0, 0.1), (0, 0.2), (0, 0.5), (1, 3.0), (1, 5.0), (1, 10.0)]
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+    from paper_2412_10789_gb300 import build, gp as gpmod
+    build.build()
+    assert torch.cuda.is_available()
+    return gpmod
+
+
+_G = {}
+
+
+def graph(name):
+    if name not in _G:
+        _G[name] = {"rmat14": lambda: gg.rmat(14, 16, seed=2), "er4096": lambda: gg.erdos_renyi(4096, 16384, 1),
+                    "chunglu20k": lambda: gg.chung_lu(20011, 30.0, 2.1, seed=4)}[name]()
+    return _G[name]
+
+
+def _outputs(g, count, device=True):
+    import torch
+    return [torch.empty(g.n, dtype=torch.float64, device="cuda" if device else "cpu") for _ in range(count)]
+
+
+def _requests(gp, g, srcs, tol, ys, k_rule=None, K=None):
+    reqs = []
+    for i, s in enumerate(srcs):
+        fn, p = MIX[i % len(MIX)]
+        if k_rule is None:
+            reqs.append(gp.make_request(fn, int(s), p, tol, ys[i]))
+        else:
+            reqs.append(gp.make_request(fn, int(s), p, tol, ys[i], k_rule=k_rule, k_fixed=K[i]))
+    return reqs
+
+
+@pytest.mark.parametrize("B", [8, 64, 256])
+def test_batch_fixed_K_parity_fp32(gp, B):
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=B)
+    try:
+        srcs = list(gg.sources(g, 20, 7)) + [int(gg.top_degree_sources(g, 1)[0])]
+        ys = _outputs(g, len(srcs))
+        Ks = [12 + (i % 9) for i in range(len(srcs))]
+        infos = gp.gp_batch(dg, _requests(gp, g, srcs, 1e-6, ys, gp.GP_K_FIXED, Ks))
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            want = O.chebypower(g, int(s), KINDS[fn], p, Ks[i])
+            e = O.errors(g, want, ys[i].cpu().numpy())
+            assert infos[i]["K"] == Ks[i]
+            assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7, (i, e)
+    finally:
+        dg.close()
+
+
+@pytest.mark.parametrize("gname", ["rmat14", "chunglu20k"])
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-6), ("f32", 1e-4), ("bf16", 1e-4), ("f16", 1e-4)])
+def test_batch_stop_rule_accuracy(gp, gname, storage, tol):
+    g = graph(gname)
+    st = {"f32": gp.GP_F32, "bf16": gp.GP_BF16, "f16": gp.GP_F16}[storage]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=32, storage=st)
+    try:
+        srcs = gg.sources(g, 40, 11)  # two blocks of 32
+        ys = _outputs(g, len(srcs))
+        infos = gp.gp_batch(dg, _requests(gp, g, srcs, tol, ys))
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            ystar = O.chebypower(g, int(s), KINDS[fn], p, 150)
+            l1 = O.errors(g, ystar, ys[i].cpu().numpy())["l1"]
+            assert l1 <= tol, (i, storage, l1, infos[i])
+    finally:
+        dg.close()
+
+
+def test_batch_host_outputs_and_isolated_source(gp):
+    g = gg.from_edges(40, [(i, i + 1) for i in range(30)] + [(35, 36)], "path_with_isolated")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=8)
+    try:
+        ys = [np.zeros(g.n, dtype=np.float64) for _ in range(3)]
+        ys.append(np.zeros(g.n, dtype=np.float32))
+        reqs = [gp.make_request(0, 3, 0.2, 1e-8, ys[0]), gp.make_request(1, 33, 4.0, 1e-8, ys[1]),
+                gp.make_request(0, 36, 0.3, 1e-8, ys[2]), gp.make_request(1, 10, 2.0, 1e-8, ys[3])]
+        gp.gp_batch(dg, reqs)
+        assert np.array_equal(ys[1], np.exp(-4.0) * O.unit_vector(g.n, 33))  # node 33 is isolated
+        for y, (k, s, p) in ((ys[0], ("ppr", 3, 0.2)), (ys[2], ("ppr", 36, 0.3)), (ys[3], ("hkpr", 10, 2.0))):
+            assert O.errors(g, O.chebypower(g, s, k, p, 200), y)["l1"] <= 1e-6
+    finally:
+        dg.close()
+
+
+def _serve_all(gp, dg, reqs, timeout=120.0):
+    tickets = [gp.gp_submit(dg, r) for r in reqs]
+    infos = [None] * len(tickets)
+    t0 = time.time()
+    while any(i is None for i in infos):
+        for j, t in enumerate(tickets):
+            if infos[j] is None:
+                infos[j] = gp.gp_poll(dg, t)
+        assert time.time() - t0 < timeout, "serving did not finish"
+        time.sleep(0.002)
+    return infos
+
+
+def test_serving_matches_oracle_and_alone(gp):
+    g = graph("rmat14")
+    srcs = gg.sources(g, 48, 19)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16)
+    try:
+        ys = _outputs(g, len(srcs))
+        reqs = []
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            tol = [1e-4, 1e-5, 1e-6][i % 3]
+            reqs.append(gp.make_request(fn, int(s), p, tol, ys[i]))
+        infos = _serve_all(gp, dg, reqs)
+        stats = gp.gp_serve_stats(dg)
+        assert stats["completed"] == len(srcs)
+        assert stats["mean_active"] > 1.0  # the queries shared passes
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            tol = [1e-4, 1e-5, 1e-6][i % 3]
+            ystar = O.chebypower(g, int(s), KINDS[fn], p, 150)
+            assert O.errors(g, ystar, ys[i].cpu().numpy())["l1"] <= tol, (i, infos[i])
+        # the same query alone in the service gives the same vector
+        for i in (0, 7, 29):
+            fn, p = MIX[i % len(MIX)]
+            tol = [1e-4, 1e-5, 1e-6][i % 3]
+            y1 = _outputs(g, 1)[0]
+            info1 = _serve_all(gp, dg, [gp.make_request(fn, int(srcs[i]), p, tol, y1)])[0]
+            assert info1["K"] == infos[i]["K"]
+            assert np.array_equal(y1.cpu().numpy(), ys[i].cpu().numpy())
+    finally:
+        dg.close()
+
+
+def test_serving_errors(gp):
+    g = graph("er4096")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=8)
+    try:
+        import torch
+        y = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        with pytest.raises(gp.GPError) as ei:
+            gp.gp_submit(dg, gp.make_request(0, g.n + 5, 0.2, 1e-6, y))
+        assert ei.value.status == gp.GP_EINVAL
+        with pytest.raises(gp.GPError) as ei:
+            gp.gp_poll(dg, 987654321)
+        assert ei.value.status == gp.GP_ENOTFOUND
+        t = gp.gp_submit(dg, gp.make_request(1, 0, 5.0, 1e-6, y))
+        info = None
+        t0 = time.time()
+        while info is None and time.time() - t0 < 60:
+            info = gp.gp_poll(dg, t)
+        assert info is not None and info["K"] > 0
+        with pytest.raises(gp.GPError):  # collected tickets are gone
+            gp.gp_poll(dg, t)
+    finally:
+        dg.close()
+
+
+def test_destroy_with_pending_tickets(gp):
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=8)
+    ys = _outputs(g, 30)
+    for i, s in enumerate(gg.sources(g, 30, 3)):
+        gp.gp_submit(dg, gp.make_request(0, int(s), 0.1, 1e-6, ys[i]))
+    dg.close()  # must not hang or fault with work queued and in flight
