@@ -57,7 +57,70 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--power-baseline", action="store_true", help="also time the GPU PwMethod")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched and served forms")
+    p.add_argument("--batch-width", type=int, default=128)
     return p.parse_args()
+
+
+def bench_batched(gp, dg_single, g, queries, dev, world, reps=3):
+    """gp_batch over the step's queries as one block: BF16 storage (FP32 warm-up)
+    at l1 <= 1e-4, and FP32 storage at l1 <= 1e-6; queries/s over `reps` runs."""
+    import torch
+    res = {}
+    for name, storage, tol in (("bf16_tol1e-4", gp.GP_BF16, 1e-4), ("fp32_tol1e-6", gp.GP_F32, 1e-6)):
+        dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=storage,
+                                block_width=min(256, len(queries)))
+        ys = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in queries]
+        reqs = [gp.make_request(fn, s, p, tol, ys[i]) for i, (fn, s, p) in enumerate(queries)]
+        infos = gp.gp_batch(dg, reqs)  # warm-up (allocates the blocks)
+        torch.cuda.synchronize()
+        dist_barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            infos = gp.gp_batch(dg, reqs)
+        torch.cuda.synchronize()
+        dt = dist_max(time.perf_counter() - t0, world, dev)
+        res[name] = {"value": len(queries) * reps * world / dt, "unit": UNIT, "block_width": len(queries),
+                     "mean_K": float(np.mean([i["K"] for i in infos]))}
+        dg.close()
+        del ys
+    return res
+
+
+def bench_serving(gp, g, queries, dev, world, reps=2):
+    """The step's queries through gp_submit/gp_poll, all submitted at once, with
+    l1 tolerances cycling over 1e-4, 1e-5, 1e-6: queries/s and latency
+    (submit to completion) percentiles."""
+    import torch
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=min(256, len(queries)))
+    ys = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in queries]
+    tols = [1e-4, 1e-5, 1e-6]
+    reqs = [gp.make_request(fn, s, p, tols[i % 3], ys[i]) for i, (fn, s, p) in enumerate(queries)]
+
+    def run_once():
+        tickets = [gp.gp_submit(dg, r) for r in reqs]
+        infos = [None] * len(tickets)
+        left = len(tickets)
+        while left:
+            for j, t in enumerate(tickets):
+                if infos[j] is None:
+                    infos[j] = gp.gp_poll(dg, t)
+                    left -= infos[j] is not None
+            time.sleep(0.0005)
+        return infos
+
+    run_once()  # warm-up
+    dist_barrier(world)
+    lat = []
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        lat += [i["ms"] for i in run_once()]
+    dt = dist_max(time.perf_counter() - t0, world, dev)
+    stats = gp.gp_serve_stats(dg)
+    dg.close()
+    return {"value": len(queries) * reps * world / dt, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_active_columns": stats["mean_active"],
+            "storage": "fp32", "arrivals": "all queries of a step submitted at once"}
 
 
 # ----------------------------------------------------------------- distributed helpers
@@ -321,6 +384,9 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         power = {"value": len(queries) / dt, "unit": UNIT, "what": "Algorithm 1 on the same GPU, same queries"}
+    # ---- batched and served forms on the same graph and queries
+    batched = None if args.no_batched else bench_batched(gp, dg, g, queries, dev, world)
+    serving = None if args.no_batched else bench_serving(gp, g, queries, dev, world)
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -347,6 +413,10 @@ def run_ours(args, rank, world):
         }
         if power:
             out["gpu_power_baseline"] = power
+        if batched:
+            out["batched"] = batched
+        if serving:
+            out["serving"] = serving
         print(json.dumps(out), flush=True)
     dg.close()
     if world > 1:

@@ -77,6 +77,10 @@ typedef struct {
   int32_t t_heavy;         /* rows with degree >= t_heavy are summed in pieces by several warps
                               (0: only rows too long for one whole-row task, > 508 entries) */
   int32_t row_ptr_64;      /* 1: keep 64-bit row offsets even when nnz fits 32 bits (default 0) */
+  int32_t precise_rows;    /* single queries on graphs with at most this many non-isolated nodes
+                              keep T_k as float pairs (~48 bits) instead of FP32: FP32 rounding
+                              is not damped on tiny graphs with unit-modulus eigenvalues
+                              (0: default 1024; -1: never) */
   double warmup_tail;      /* 16-bit storage only once tail(k) < warmup_tail (default 1e-2) */
   size_t mem_budget;       /* bytes the serving loop may use for column blocks (0: 80% of free) */
   void* (*alloc)(size_t bytes, void* ctx); /* device allocator; NULL: cudaMalloc */

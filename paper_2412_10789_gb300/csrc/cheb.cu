@@ -240,8 +240,23 @@ static void run_single(Graph& g, const gp_request& req, gp_query_info* info, boo
     taylor_coefficients(req.function, req.param, req.l1_tol, kPassCap, c);
     tail.assign(kPassCap + 1, -1.0);
   }
-  // ---- init
   const int64_t s = g.h_newid[req.source];
+  if (use_precise(g)) {
+    // tiny graph: float-pair storage of Q (precise.cu)
+    double C = 1.0;
+    const int K = run_precise(g, s, cheb, c, tail, cheb ? k_fixed : (int)c.size() - 1, req.l1_tol, kcap, &C);
+    emit_output(g, req, false, f0);
+    if (sync_needed) GP_CUDA_TRY(cudaStreamSynchronize(g.stream));
+    if (info) {
+      info->K = K;
+      info->k16_from = K + 1;
+      info->max_r_l1 = cheb ? C : 1.0;
+      info->tail_bound = cheb && K < (int)tail.size() ? tail[K] * C : 0.0;
+      info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return;
+  }
+  // ---- init
   GP_CUDA_TRY(cudaMemsetAsync(w.qa, 0, sizeof(float) * g.n_active, g.stream));
   GP_CUDA_TRY(cudaMemsetAsync(w.qb, 0, sizeof(float) * g.n_active, g.stream));
   GP_CUDA_TRY(cudaMemsetAsync(w.y, 0, sizeof(float2) * g.n, g.stream));

@@ -169,6 +169,12 @@ void free_schedule(Graph& g);
 // Bytes one fused step must move for one column (algorithmic traffic).
 double step_bytes_single(const Graph& g);
 
+// precise.cu: the float-pair storage path for graphs of at most
+// cfg.precise_rows active rows; returns K and max_l ||r_l||_1.
+bool use_precise(const Graph& g);
+int run_precise(Graph& g, int64_t s, bool cheb, const std::vector<double>& c, const std::vector<double>& tail,
+                int k_fixed, double tol, int kcap, double* C_out);
+
 // cheb.cu
 void run_query(Graph& g, const gp_request& req, gp_query_info* info);
 void run_power(Graph& g, const gp_request& req, gp_query_info* info);
@@ -235,6 +241,18 @@ __device__ __forceinline__ void ksum_add(KSum& k, float v) {
 // Merge two compensated sums into one float pair (hi, lo), value s1 - c1 + s2 - c2.
 __device__ __forceinline__ DF ksum_merge(DF a, DF b) { return df_add(a, b); }
 __device__ __forceinline__ DF ksum_value(const KSum& k) { return df_two_sum(k.s, -k.c); }
+// Cascaded summation with TwoSum (Ogita, Rump and Oishi's Sum2): the error of
+// every addition is captured exactly whatever the signs and magnitudes, so the
+// pair (s, c) carries about twice the working precision.
+struct S2Sum {
+  float s, c;
+};
+__device__ __forceinline__ void s2sum_add(S2Sum& k, float v) {
+  const DF t = df_two_sum(k.s, v);
+  k.s = t.hi;
+  k.c = __fadd_rn(k.c, t.lo);
+}
+__device__ __forceinline__ DF s2sum_value(const S2Sum& k) { return df_fast_two_sum(k.s, k.c); }
 #endif  // __CUDACC__
 
 }  // namespace gp

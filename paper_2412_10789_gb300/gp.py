@@ -41,6 +41,7 @@ class gp_config(ctypes.Structure):
         ("validate_symmetry", ctypes.c_int32),
         ("t_heavy", ctypes.c_int32),
         ("row_ptr_64", ctypes.c_int32),
+        ("precise_rows", ctypes.c_int32),
         ("warmup_tail", ctypes.c_double),
         ("mem_budget", ctypes.c_size_t),
         ("alloc", _ALLOC_T),

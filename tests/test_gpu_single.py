@@ -195,6 +195,23 @@ def test_edge_cases(gp):
             dg.close()
 
 
+@pytest.mark.parametrize("kind,param", [("ppr", 0.2), ("hkpr", 5.0)])
+def test_float_pair_path_parity(gp, kind, param):
+    # The float-pair storage path (used on tiny graphs) forced on a larger one:
+    # ~48-bit arithmetic, so the bar is far below the FP32 path's.
+    g = graph("rmat13")
+    dg = make(gp, g, precise_rows=1 << 20)
+    try:
+        for s in list(gg.sources(g, 2, 5)) + [int(gg.top_degree_sources(g, 1)[0])]:
+            got, info = run(gp, dg, g, kind, int(s), param, K=25)
+            e = O.errors(g, O.chebypower(g, int(s), kind, param, 25), got)
+            assert e["l1"] <= 1e-10 and e["maxabs"] <= 1e-12, e
+            got, info = run(gp, dg, g, kind, int(s), param, tol=1e-8)
+            assert O.errors(g, O.chebypower(g, int(s), kind, param, 160), got)["l1"] <= 1e-8
+    finally:
+        dg.close()
+
+
 def test_isolated_only_graph(gp):
     g = gg.from_edges(5, [])
     dg = make(gp, g)
