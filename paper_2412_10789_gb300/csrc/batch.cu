@@ -41,7 +41,17 @@ namespace {
 
 constexpr float kF16Scale = 4096.0f;
 constexpr int kChunk = 1024;       // entries per chunk of a long row
-constexpr int kBatchThreads = 256;
+#ifndef GP_SPMM_UNROLL
+#define GP_SPMM_UNROLL 4
+#endif
+#ifndef GP_SPMM_THREADS
+#define GP_SPMM_THREADS 512
+#endif
+#ifndef GP_SPMM_MINB
+#define GP_SPMM_MINB 1
+#endif
+constexpr int kBatchThreads = GP_SPMM_THREADS;
+constexpr int kSpmmUnroll = GP_SPMM_UNROLL;  // row gathers in flight per lane
 
 // ---- 8-column vectors of each storage type
 struct V8 {
@@ -84,12 +94,19 @@ struct Store<__nv_bfloat16> {
   __device__ static __forceinline__ Raw load_raw(const void* base, int64_t row, int B, int cg) {
     return __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * B + cg * 8));
   }
+  // Widen each bf16 pair to two floats (a shift and a mask) and add them to
+  // the accumulator pair with one packed FP32 add.
   __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      acc[2 * i] += __uint_as_float(u[i] << 16);
-      acc[2 * i + 1] += __uint_as_float(u[i] & 0xffff0000u);
+      const unsigned long long v =
+          ((unsigned long long)(u[i] & 0xffff0000u) << 32) | (unsigned long long)(u[i] << 16);
+      unsigned long long s =
+          ((unsigned long long)__float_as_uint(acc[2 * i + 1]) << 32) | __float_as_uint(acc[2 * i]);
+      asm("add.rn.f32x2 %0, %0, %1;" : "+l"(s) : "l"(v));
+      acc[2 * i] = __uint_as_float((uint32_t)s);
+      acc[2 * i + 1] = __uint_as_float((uint32_t)(s >> 32));
     }
   }
   __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
@@ -182,18 +199,18 @@ __device__ __forceinline__ void gather_rows(const SpmmArgs& a, int64_t lo, int64
     const int myidx = lane < ne ? __ldcs(a.ci + e0 + lane) : 0;
     // The loop is uniform across the warp (every lane reaches each shuffle);
     // lane (g, cg) takes entries j0 + g + u*EG.
-    for (int j0 = 0; j0 < ne; j0 += 4 * EG) {
-      int v[4];
+    for (int j0 = 0; j0 < ne; j0 += kSpmmUnroll * EG) {
+      int v[kSpmmUnroll];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = __shfl_sync(0xffffffffu, myidx, min(j0 + g + u * EG, 31));
-      typename Store<TG>::Raw x[4];
+      for (int u = 0; u < kSpmmUnroll; ++u) v[u] = __shfl_sync(0xffffffffu, myidx, min(j0 + g + u * EG, 31));
+      typename Store<TG>::Raw x[kSpmmUnroll];
       // (a neighbour beyond the active rows can only come from an unvalidated,
       // asymmetric CSR; its Q is zero and it is skipped)
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < kSpmmUnroll; ++u)
         if (j0 + g + u * EG < ne && v[u] < a.na) x[u] = Store<TG>::load_raw(a.qcur, v[u], a.B, cg);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < kSpmmUnroll; ++u)
         if (j0 + g + u * EG < ne && v[u] < a.na) Store<TG>::add(x[u], acc);
     }
   }
@@ -207,13 +224,28 @@ __device__ __forceinline__ void reduce_groups(float acc[8], int CG) {
   }
 }
 
+// Own-row data of one lane's 8 columns: Q_{k-1}[u] and y[u].
+struct RowOwn {
+  V8 prev;
+  float4 y0, y1;
+};
+
+template <typename TP>
+__device__ __forceinline__ RowOwn load_own(const SpmmArgs& a, int64_t u, int cg) {
+  RowOwn o;
+  o.prev = Store<TP>::load(a.qprev, u, a.B, cg);
+  const float* yrow = a.y + u * a.B + cg * 8;
+  o.y0 = *reinterpret_cast<const float4*>(yrow);
+  o.y1 = *reinterpret_cast<const float4*>(yrow + 4);
+  return o;
+}
+
 template <typename TP, typename TO>
 __device__ __forceinline__ void update_row(const SpmmArgs& a, const ColState* s_col, int64_t u, float d, int cg,
-                                           const float acc[8], float nrm[8]) {
-  const V8 prev = Store<TP>::load(a.qprev, u, a.B, cg);
+                                           const float acc[8], const RowOwn& own, float nrm[8]) {
+  const V8& prev = own.prev;
   float* yrow = a.y + u * a.B + cg * 8;
-  float4 y0 = *reinterpret_cast<const float4*>(yrow), y1 = *reinterpret_cast<const float4*>(yrow + 4);
-  float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+  float yv[8] = {own.y0.x, own.y0.y, own.y0.z, own.y0.w, own.y1.x, own.y1.y, own.y1.z, own.y1.w};
   V8 out = prev;
   const float inv = 1.0f / d;
 #pragma unroll
@@ -232,7 +264,7 @@ __device__ __forceinline__ void update_row(const SpmmArgs& a, const ColState* s_
 }
 
 template <typename RP, typename TG, typename TP, typename TO>
-__global__ void __launch_bounds__(kBatchThreads, 3) spmm_step_kernel(const __grid_constant__ SpmmArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, GP_SPMM_MINB) spmm_step_kernel(const __grid_constant__ SpmmArgs a) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   ColState* s_col = reinterpret_cast<ColState*>(s_raw);
   float* s_norm = reinterpret_cast<float*>(s_raw + sizeof(ColState) * a.B);
@@ -253,9 +285,11 @@ __global__ void __launch_bounds__(kBatchThreads, 3) spmm_step_kernel(const __gri
     const int64_t beg = rp[row], end = rp[row + 1];
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (unit.y < 0) {
+      RowOwn own{};
+      if (g == 0) own = load_own<TP>(a, row, cg);  // in flight during the gathers
       gather_rows<TG, RP>(a, beg, end, g, EG, cg, acc);
       reduce_groups(acc, CG);
-      if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, acc, nrm);
+      if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, acc, own, nrm);
     } else {
       const int p = unit.y;
       const int64_t lo = beg + (int64_t)p * kChunk, hi = min(lo + (int64_t)kChunk, end);
@@ -285,7 +319,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) spmm_step_kernel(const __gri
         }
         reduce_groups(tot, CG);
         if (lane == 0) a.cnt[row] = 0;
-        if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, tot, nrm);
+        if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, tot, load_own<TP>(a, row, cg), nrm);
       }
     }
   }
