@@ -23,7 +23,6 @@ with the same per-GPU work (weak scaling, no data-path collective).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -40,8 +39,6 @@ import numpy as np  # noqa: E402
 METRIC = "PPR/HKPR queries/s at l1<=1e-6 (single-source ChebyPower, R-MAT scale 22)"
 UNIT = "queries/s"
 PROFILE_FILE = os.path.join(ROOT, "profiles", "cheb_step_rmat22.json")
-STEP_KERNEL_SOURCES = [os.path.join(ROOT, "paper_2412_10789_gb300", "csrc", f)
-                       for f in ("cheb.cu", "gp_internal.h")]
 
 
 def parse():
@@ -165,14 +162,6 @@ def workload(scale, nsrc):
     return g, queries
 
 
-def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in STEP_KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
 def ncu_traffic():
     """dram bytes per launch of the step kernel from the committed ncu summary,
     or None when absent or taken on different kernel source."""
@@ -181,7 +170,8 @@ def ncu_traffic():
             prof = json.load(f)
     except (OSError, ValueError):
         return None
-    if prof.get("kernel_source_hash") != kernel_source_hash():
+    from paper_2412_10789_gb300.ncu_summary import source_hash
+    if prof.get("kernel_source_hash") != source_hash(prof.get("kernel", "cheb_step_kernel")):
         return None
     return prof.get("dram_bytes_per_launch_full_size")
 
