@@ -11,6 +11,14 @@
 // Each edge gathers a whole B*s-byte row, so the block amortises the col_idx
 // stream over B columns and uses every byte of the sectors it reads.
 //
+// The pass is bound by the latency of those gathers, so the kernel keeps many
+// of them in flight without holding them in registers: each warp streams
+// tiles of consecutive col_idx entries (staged in shared memory one tile
+// ahead) and copies the gathered row segments with cp.async into a per-warp
+// ring in shared memory, S rounds ahead of the lanes that add them up.  The
+// own row's Q_{k-1} and y segments travel through the same ring after the
+// row's gathers, so no step of a row waits on a dependent global load.
+//
 // Columns are independent queries: each has its own function, coefficient
 // table, tail, tolerance, step k and stop state (per-column stop rule of
 // Theorem 1 read for l1, as in the single query).  A control kernel between
@@ -40,18 +48,71 @@ namespace gp {
 namespace {
 
 constexpr float kF16Scale = 4096.0f;
-constexpr int kChunk = 1024;       // entries per chunk of a long row
-#ifndef GP_SPMM_UNROLL
-#define GP_SPMM_UNROLL 4
-#endif
+
+// ---- schedule of the batched pass
+// The pass walks tiles of consecutive col_idx entries (built per engine from
+// the relabelled, degree-descending rows):
+//   kind 0, rows per group: nrows rows of equal degree d; the lane groups of
+//           a warp take one row each (rows g, g + EG, ...), no reduction;
+//   kind 1, rows per warp:  nrows rows of equal degree d, each row's entries
+//           split over the EG lane groups and combined by shuffles;
+//   kind 2, chunk:          len entries of one long row (chunk p); the warp
+//           that finishes the row's last chunk adds the chunk partials in
+//           chunk order and updates the row.
+// Descriptor int4 {row0, e0 low, e0 high, meta}: meta bits 0-1 kind,
+// bits 2-16 nrows (kinds 0, 1) or p (kind 2), bits 17-31 d or len.
+constexpr int kBTileCap = 508;   // entries of a tile (room for 16-byte alignment in kBTileSpan)
+constexpr int kBTileSpan = 512;  // staged indices per buffer
+constexpr int kBTileCost = 512;  // rows tiles: nrows * (d + 3) at most
 #ifndef GP_SPMM_THREADS
 #define GP_SPMM_THREADS 512
 #endif
-#ifndef GP_SPMM_MINB
-#define GP_SPMM_MINB 1
+#ifndef GP_SPMM_RING
+#define GP_SPMM_RING 256
 #endif
-constexpr int kBatchThreads = GP_SPMM_THREADS;
-constexpr int kSpmmUnroll = GP_SPMM_UNROLL;  // row gathers in flight per lane
+constexpr int kBatchThreads = GP_SPMM_THREADS;  // one persistent CTA per SM
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kRingLaneBytes = GP_SPMM_RING;    // per lane: bytes of gathers in flight
+constexpr int kHeaderBytes = 256 * 12;          // ColState + norm of up to 256 columns
+constexpr size_t kSpmmSmem =
+    kHeaderBytes + (size_t)kBatchWarps * (32 * kRingLaneBytes + 2 * kBTileSpan * sizeof(int));
+
+__host__ __device__ inline int4 make_btile(int64_t row0, int64_t e0, int kind, int a, int b) {
+  const uint32_t meta = (uint32_t)kind | ((uint32_t)a << 2) | ((uint32_t)b << 17);
+  return make_int4((int)row0, (int)(uint32_t)(e0 & 0xffffffffu), (int)(e0 >> 32), (int)meta);
+}
+
+struct BTile {
+  int64_t row0, e0;
+  int kind, a, b;
+};
+
+__device__ __forceinline__ BTile decode_btile(int4 t) {
+  const uint32_t m = (uint32_t)t.w;
+  return BTile{t.x, (int64_t)(uint32_t)t.y | ((int64_t)t.z << 32), (int)(m & 3u), (int)((m >> 2) & 0x7fffu),
+               (int)(m >> 17)};
+}
+
+// ---- cache policies and asynchronous copies
+__device__ __forceinline__ uint64_t bpolicy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t bpolicy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bcp16(uint32_t dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void bcommit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bwait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // ---- 8-column vectors of each storage type
 struct V8 {
@@ -67,9 +128,8 @@ struct Store<float> {
   struct Raw {
     float4 a, b;
   };
-  __device__ static __forceinline__ Raw load_raw(const void* base, int64_t row, int B, int cg) {
-    const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(base) + row * B + cg * 8);
-    return Raw{__ldg(p), __ldg(p + 1)};
+  __device__ static __forceinline__ Raw lds(const unsigned char* p) {
+    return Raw{*reinterpret_cast<const float4*>(p), *reinterpret_cast<const float4*>(p + 16)};
   }
   __device__ static __forceinline__ void add(const Raw& r, float acc[8]) {
     acc[0] += r.a.x; acc[1] += r.a.y; acc[2] += r.a.z; acc[3] += r.a.w;
@@ -91,9 +151,7 @@ template <>
 struct Store<__nv_bfloat16> {
   static constexpr int bytes = 2;
   using Raw = uint4;
-  __device__ static __forceinline__ Raw load_raw(const void* base, int64_t row, int B, int cg) {
-    return __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * B + cg * 8));
-  }
+  __device__ static __forceinline__ Raw lds(const unsigned char* p) { return *reinterpret_cast<const uint4*>(p); }
   // Widen each bf16 pair to two floats (a shift and a mask) and add them to
   // the accumulator pair with one packed FP32 add.
   __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
@@ -109,15 +167,17 @@ struct Store<__nv_bfloat16> {
       acc[2 * i + 1] = __uint_as_float((uint32_t)(s >> 32));
     }
   }
-  __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
-    const uint4 w = __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * B + cg * 8));
+  __device__ static __forceinline__ void decode(const Raw& w, float v[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-    V8 v;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      v.x[2 * i] = __uint_as_float(u[i] << 16);
-      v.x[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+      v[2 * i] = __uint_as_float(u[i] << 16);
+      v[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
     }
+  }
+  __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
+    V8 v;
+    decode(__ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * B + cg * 8)), v.x);
     return v;
   }
   __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
@@ -135,28 +195,28 @@ template <>
 struct Store<__half> {
   static constexpr int bytes = 2;
   using Raw = uint4;
-  __device__ static __forceinline__ Raw load_raw(const void* base, int64_t row, int B, int cg) {
-    return __ldg(reinterpret_cast<const uint4*>(static_cast<const __half*>(base) + row * B + cg * 8));
-  }
+  __device__ static __forceinline__ Raw lds(const unsigned char* p) { return *reinterpret_cast<const uint4*>(p); }
   __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[i]));
-      acc[2 * i] += f.x * (1.0f / kF16Scale);
-      acc[2 * i + 1] += f.y * (1.0f / kF16Scale);
+      acc[2 * i] = fmaf(f.x, 1.0f / kF16Scale, acc[2 * i]);
+      acc[2 * i + 1] = fmaf(f.y, 1.0f / kF16Scale, acc[2 * i + 1]);
     }
   }
-  __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
-    const uint4 w = __ldg(reinterpret_cast<const uint4*>(static_cast<const __half*>(base) + row * B + cg * 8));
+  __device__ static __forceinline__ void decode(const Raw& w, float v[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-    V8 v;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[i]));
-      v.x[2 * i] = f.x * (1.0f / kF16Scale);
-      v.x[2 * i + 1] = f.y * (1.0f / kF16Scale);
+      v[2 * i] = f.x * (1.0f / kF16Scale);
+      v[2 * i + 1] = f.y * (1.0f / kF16Scale);
     }
+  }
+  __device__ static __forceinline__ V8 load(const void* base, int64_t row, int B, int cg) {
+    V8 v;
+    decode(__ldg(reinterpret_cast<const uint4*>(static_cast<const __half*>(base) + row * B + cg * 8)), v.x);
     return v;
   }
   __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
@@ -171,163 +231,429 @@ struct Store<__half> {
 };
 
 struct SpmmArgs {
-  const int2* units;   // {row, chunk index or -1}
-  int64_t nunits;
-  const void* rp;
+  const int4* tiles;
+  int64_t ntiles;
   const int32_t* ci;
-  const void* qcur;    // Q_k  (gather type)
-  const void* qprev;   // Q_{k-1} (prev type)
-  void* qnext;         // Q_{k+1} (out type); equals qprev when the types match
-  float* y;            // n_active x B
-  const ColState* col; // per column: active flag and coefficient of this pass
-  float* norm;         // per column ||r_{k+1}||_1 of this pass
-  const int* poff;     // long rows: first chunk slot
-  float* part;         // long rows: chunk partial sums, [slot][B]
-  int* cnt;            // long rows: chunks finished
-  int64_t na;          // rows of the blocks (nodes with degree >= 1)
+  const void* qcur;     // Q_k  (gather type)
+  const void* qprev;    // Q_{k-1} (prev type)
+  void* qnext;          // Q_{k+1} (out type); equals qprev when the types match
+  float* y;             // n_active x B
+  const ColState* col;  // per column: active flag and coefficient of this pass
+  float* norm;          // per column ||r_{k+1}||_1 of this pass
+  const int* poff;      // long rows: first chunk slot
+  const int64_t* ldeg;  // long rows: degree
+  float* part;          // long rows: chunk partial sums, [slot][B]
+  int* cnt;             // long rows: chunks finished
+  const void* zero;     // B zero values: the gather source of a neighbour beyond the active rows
+  int64_t na;           // rows of the blocks (nodes with degree >= 1)
   int B;
 };
 
-// Sum over neighbours of row `row` in [lo, hi): this lane accumulates its 8
-// columns (group cg) over the entries of its entry group g.
-template <typename TG, typename RP>
-__device__ __forceinline__ void gather_rows(const SpmmArgs& a, int64_t lo, int64_t hi, int g, int EG, int cg,
-                                            float acc[8]) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t e0 = lo; e0 < hi; e0 += 32) {
-    const int ne = (int)min((int64_t)32, hi - e0);
-    const int myidx = lane < ne ? __ldcs(a.ci + e0 + lane) : 0;
-    // The loop is uniform across the warp (every lane reaches each shuffle);
-    // lane (g, cg) takes entries j0 + g + u*EG.
-    for (int j0 = 0; j0 < ne; j0 += kSpmmUnroll * EG) {
-      int v[kSpmmUnroll];
-#pragma unroll
-      for (int u = 0; u < kSpmmUnroll; ++u) v[u] = __shfl_sync(0xffffffffu, myidx, min(j0 + g + u * EG, 31));
-      typename Store<TG>::Raw x[kSpmmUnroll];
-      // (a neighbour beyond the active rows can only come from an unvalidated,
-      // asymmetric CSR; its Q is zero and it is skipped)
-#pragma unroll
-      for (int u = 0; u < kSpmmUnroll; ++u)
-        if (j0 + g + u * EG < ne && v[u] < a.na) x[u] = Store<TG>::load_raw(a.qcur, v[u], a.B, cg);
-#pragma unroll
-      for (int u = 0; u < kSpmmUnroll; ++u)
-        if (j0 + g + u * EG < ne && v[u] < a.na) Store<TG>::add(x[u], acc);
-    }
-  }
-}
-
 // Combine the entry groups' partial sums (lanes cg, cg + CG, cg + 2 CG, ...).
-__device__ __forceinline__ void reduce_groups(float acc[8], int CG) {
+template <int LC>
+__device__ __forceinline__ void reduce_groups(float acc[LC], int CG) {
   for (int off = CG; off < 32; off <<= 1) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+    for (int i = 0; i < LC; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
   }
 }
 
-// Own-row data of one lane's 8 columns: Q_{k-1}[u] and y[u].
-struct RowOwn {
-  V8 prev;
-  float4 y0, y1;
+// Compile-time geometry of one kernel instance: a lane owns LC consecutive
+// columns; one ring round moves SB bytes per lane.
+template <typename TG, typename TP, typename TO, int LC>
+struct Geo {
+  static constexpr int sG = Store<TG>::bytes, sP = Store<TP>::bytes;
+  static constexpr int SB = LC * sG;              // bytes of a gathered segment
+  static constexpr int S = kRingLaneBytes / SB;   // rounds in flight
+  static constexpr int OP = LC * sP / SB;         // rounds of the own Q_{k-1} segment (1 or 2)
+  static constexpr int OY = LC * 4 / SB;          // rounds of the own y segment (1 or 2)
+  static constexpr int PW = SB / 4;               // floats per round of an FP32 segment
+  static_assert(S >= 2 && (S & (S - 1)) == 0, "ring depth must be a power of two");
+  static_assert(SB == 16 || SB == 32, "a round moves 16 or 32 bytes per lane");
 };
 
-template <typename TP>
-__device__ __forceinline__ RowOwn load_own(const SpmmArgs& a, int64_t u, int cg) {
-  RowOwn o;
-  o.prev = Store<TP>::load(a.qprev, u, a.B, cg);
-  const float* yrow = a.y + u * a.B + cg * 8;
-  o.y0 = *reinterpret_cast<const float4*>(yrow);
-  o.y1 = *reinterpret_cast<const float4*>(yrow + 4);
-  return o;
+// Per-lane constants of the pass.
+struct Lane {
+  const SpmmArgs* a;
+  const ColState* s_col;
+  uint32_t ring;               // shared address of this lane's slot 0
+  const unsigned char* ring_p; // the same, generic
+  const unsigned char* qcur;   // Q_k
+  const unsigned char* zero;   // zero segment
+  size_t rowG, rowP, segG, segP;
+  uint64_t pol_keep, pol_stream;
+  int cg, g, CG, EG, lane;
+};
+
+// Add one gathered segment (LC values of TG) from a ring slot.
+template <typename TG, int LC>
+__device__ __forceinline__ void add_seg(const unsigned char* p, float acc[LC]) {
+#pragma unroll
+  for (int h = 0; h < LC / 8; ++h) Store<TG>::add(Store<TG>::lds(p + h * 8 * Store<TG>::bytes), acc + 8 * h);
 }
 
-template <typename TP, typename TO>
-__device__ __forceinline__ void update_row(const SpmmArgs& a, const ColState* s_col, int64_t u, float d, int cg,
-                                           const float acc[8], const RowOwn& own, float nrm[8]) {
-  const V8& prev = own.prev;
-  float* yrow = a.y + u * a.B + cg * 8;
-  float yv[8] = {own.y0.x, own.y0.y, own.y0.z, own.y0.w, own.y1.x, own.y1.y, own.y1.z, own.y1.w};
-  V8 out = prev;
-  const float inv = 1.0f / d;
+// Piece o of an LC-float segment (PW floats per piece) from a ring slot.
+template <int LC, int PW>
+__device__ __forceinline__ void put_f32(float v[LC], int o, const unsigned char* src) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  if constexpr (PW == LC) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const ColState& cs = s_col[cg * 8 + i];
-    if (cs.active) {
-      const float r = 2.0f * acc[i] - d * prev.x[i];
-      out.x[i] = r * inv;
-      yv[i] = fmaf(cs.coef, r, yv[i]);
-      nrm[i] += fabsf(r);
+    for (int i = 0; i < LC / 4; ++i) {
+      const float4 x = s4[i];
+      v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+    }
+  } else {
+    static_assert(2 * PW == LC, "one or two pieces per segment");
+#pragma unroll
+    for (int i = 0; i < PW / 4; ++i) {
+      const float4 x = s4[i];
+      if (o == 0) {
+        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+      } else {
+        v[PW + 4 * i] = x.x; v[PW + 4 * i + 1] = x.y; v[PW + 4 * i + 2] = x.z; v[PW + 4 * i + 3] = x.w;
+      }
     }
   }
-  Store<TO>::store(a.qnext, u, a.B, cg, out);
-  *reinterpret_cast<float4*>(yrow) = make_float4(yv[0], yv[1], yv[2], yv[3]);
-  *reinterpret_cast<float4*>(yrow + 4) = make_float4(yv[4], yv[5], yv[6], yv[7]);
 }
 
-template <typename RP, typename TG, typename TP, typename TO>
-__global__ void __launch_bounds__(kBatchThreads, GP_SPMM_MINB) spmm_step_kernel(const __grid_constant__ SpmmArgs a) {
+// Piece o of the own Q_{k-1} segment.
+template <typename TP, int LC, int PW>
+__device__ __forceinline__ void put_prev(float prev[LC], int o, const unsigned char* src) {
+  if constexpr (Store<TP>::bytes == 4) {
+    put_f32<LC, PW>(prev, o, src);
+  } else {  // a 16-bit segment always fits one round
+#pragma unroll
+    for (int h = 0; h < LC / 8; ++h) Store<TP>::decode(Store<TP>::lds(src + 16 * h), prev + 8 * h);
+  }
+}
+
+// Row u's update from its neighbour sums acc, Q_{k-1}(u) (prev) and y(u) for
+// this lane's LC columns: r = 2 acc - d prev, Q_{k+1} = r / d, y += c r.
+// Retired columns keep their values (y final; Q copied).
+template <typename TO, int LC>
+__device__ __forceinline__ void update_seg(const Lane& L, int64_t u, float d, const float acc[LC],
+                                           const float prev[LC], float yv[LC], float nrm[LC]) {
+  const SpmmArgs& a = *L.a;
+  const float inv = 1.0f / d;
+#pragma unroll
+  for (int h = 0; h < LC / 8; ++h) {
+    V8 out;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = 8 * h + i;
+      const ColState& cs = L.s_col[L.cg * LC + c];
+      out.x[i] = prev[c];
+      if (cs.active) {
+        const float r = 2.0f * acc[c] - d * prev[c];
+        out.x[i] = r * inv;
+        yv[c] = fmaf(cs.coef, r, yv[c]);
+        nrm[c] += fabsf(r);
+      }
+    }
+    Store<TO>::store(a.qnext, u, a.B, L.cg * (LC / 8) + h, out);
+  }
+  float4* yrow = reinterpret_cast<float4*>(a.y + u * a.B + L.cg * LC);
+#pragma unroll
+  for (int i = 0; i < LC / 4; ++i) yrow[i] = make_float4(yv[4 * i], yv[4 * i + 1], yv[4 * i + 2], yv[4 * i + 3]);
+}
+
+// Copy a tile's col_idx entries [e0, e0 + len) into a warp's staging buffer
+// with 16-byte copies from the aligned-down start; entry e0 + i lands at
+// index (e0 & 3) + i.  (col_idx is padded so the last vector is in bounds.)
+__device__ __forceinline__ void stage_indices(int* buf, const int32_t* ci, int64_t e0, int len, int lane,
+                                              uint64_t pol) {
+  const int64_t a0 = e0 & ~(int64_t)3;
+  const int nvec = (int)((e0 + len - a0 + 3) >> 2);
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
+  for (int v = lane; v < nvec; v += 32) bcp16(base + 16u * v, ci + a0 + 4 * v, pol);
+}
+
+__device__ __forceinline__ int tile_len(const BTile& t) { return t.kind == 2 ? t.b : t.a * t.b; }
+
+template <int SB>
+__device__ __forceinline__ void cp_seg(uint32_t dst, const unsigned char* src, uint64_t pol) {
+#pragma unroll
+  for (int h = 0; h < SB / 16; ++h) bcp16(dst + 16 * h, src + 16 * h, pol);
+}
+
+// Kind 0 tile: lane group g takes rows g, g + EG, ... of the tile; a row is d
+// gather rounds, then OP rounds of its Q_{k-1} segment and OY of its y
+// segment.  The caller has issued the next tile's index copies, which join
+// round 0's copy group.
+template <typename TG, typename TP, typename TO, int LC>
+__device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
+  using C = Geo<TG, TP, TO, LC>;
+  constexpr int S = C::S, SB = C::SB, OP = C::OP;
+  const SpmmArgs& a = *L.a;
+  const int d = t.b, nrows = t.a, EG = L.EG;
+  const int rpr = d + C::OP + C::OY;
+  const int nseq = (nrows + EG - 1) / EG;
+  const int R = nseq * rpr;
+  // producer: sequence ps, round pt, next index pj; consumer: sequence cs, round ct
+  int ps = 0, pt = 0, pj = L.g * d, prow = L.g;
+  int cs = 0, ct = 0, crow = L.g;
+  auto issue = [&](int slot) {
+    if (ps < nseq) {
+      if (prow < nrows) {
+        const uint32_t dst = L.ring + (uint32_t)(slot * 32 * SB);
+        if (pt < d) {
+          const int v = ci_t[pj];
+          cp_seg<SB>(dst, v < a.na ? L.qcur + (size_t)v * L.rowG + L.segG : L.zero, L.pol_keep);
+        } else {
+          const int64_t u = t.row0 + prow;
+          const int o = pt - d;
+          const unsigned char* src =
+              o < OP ? static_cast<const unsigned char*>(a.qprev) + (size_t)u * L.rowP + L.segP + (size_t)o * SB
+                     : reinterpret_cast<const unsigned char*>(a.y + u * a.B + L.cg * LC) + (size_t)(o - OP) * SB;
+          cp_seg<SB>(dst, src, L.pol_stream);
+        }
+      }
+      ++pj;
+      if (++pt == rpr) {
+        pt = 0;
+        ++ps;
+        prow += EG;
+        pj = prow * d;
+      }
+    }
+  };
+  float acc[LC], prev[LC], yv[LC];
+#pragma unroll
+  for (int i = 0; i < LC; ++i) acc[i] = prev[i] = yv[i] = 0.f;
+#pragma unroll 1
+  for (int i = 0; i < S - 1; ++i) {
+    issue(i);
+    bcommit();
+  }
+#pragma unroll 1
+  for (int rc = 0; rc < R; ++rc) {
+    bwait<S - 2>();  // round rc has landed
+    const unsigned char* src = L.ring_p + (rc & (S - 1)) * 32 * SB;
+    const bool mine = crow < nrows;
+    if (ct < d) {
+      if (mine) add_seg<TG, LC>(src, acc);
+    } else if (ct < d + OP) {
+      if (mine) put_prev<TP, LC, C::PW>(prev, ct - d, src);
+    } else {
+      if (mine) put_f32<LC, C::PW>(yv, ct - d - OP, src);
+      if (ct == rpr - 1) {
+        if (mine) update_seg<TO, LC>(L, t.row0 + crow, (float)d, acc, prev, yv, nrm);
+#pragma unroll
+        for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+      }
+    }
+    if (++ct == rpr) {
+      ct = 0;
+      ++cs;
+      crow += EG;
+    }
+    issue((rc + S - 1) & (S - 1));
+    bcommit();
+  }
+}
+
+// Kind 1 (CHUNK false) and kind 2 (CHUNK true) tiles: the EG lane groups split
+// each row's entries (entry j of a row goes to group j % EG) and combine their
+// sums by shuffles; kind 1 rows then take OP + OY own rounds (group 0), a
+// chunk publishes its partial and the last chunk of the row updates it.
+template <typename TG, typename TP, typename TO, int LC, bool CHUNK>
+__device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
+  using C = Geo<TG, TP, TO, LC>;
+  constexpr int S = C::S, SB = C::SB, OP = C::OP;
+  const SpmmArgs& a = *L.a;
+  const int EG = L.EG, g = L.g;
+  const int d = t.b;  // entries per row (kind 1) or of the chunk (kind 2)
+  const int G = (d + EG - 1) / EG;
+  const int rpr = CHUNK ? G : G + C::OP + C::OY;
+  const int nseq = CHUNK ? 1 : t.a;
+  const int R = nseq * rpr;
+  int ps = 0, pt = 0, pj = g;
+  int cs = 0, ct = 0;
+  auto issue = [&](int slot) {
+    if (ps < nseq) {
+      const uint32_t dst = L.ring + (uint32_t)(slot * 32 * SB);
+      if (pt < G) {
+        if (pt * EG + g < d) {
+          const int v = ci_t[pj];
+          cp_seg<SB>(dst, v < a.na ? L.qcur + (size_t)v * L.rowG + L.segG : L.zero, L.pol_keep);
+        }
+        pj += EG;
+      } else if (!CHUNK && g == 0) {
+        const int64_t u = t.row0 + ps;
+        const int o = pt - G;
+        const unsigned char* src =
+            o < OP ? static_cast<const unsigned char*>(a.qprev) + (size_t)u * L.rowP + L.segP + (size_t)o * SB
+                   : reinterpret_cast<const unsigned char*>(a.y + u * a.B + L.cg * LC) + (size_t)(o - OP) * SB;
+        cp_seg<SB>(dst, src, L.pol_stream);
+      }
+      if (++pt == rpr) {
+        pt = 0;
+        ++ps;
+        pj = ps * d + g;
+      }
+    }
+  };
+  float acc[LC], prev[LC], yv[LC];
+#pragma unroll
+  for (int i = 0; i < LC; ++i) acc[i] = prev[i] = yv[i] = 0.f;
+#pragma unroll 1
+  for (int i = 0; i < S - 1; ++i) {
+    issue(i);
+    bcommit();
+  }
+#pragma unroll 1
+  for (int rc = 0; rc < R; ++rc) {
+    bwait<S - 2>();  // round rc has landed
+    const unsigned char* src = L.ring_p + (rc & (S - 1)) * 32 * SB;
+    if (ct < G) {
+      if (ct * EG + g < d) add_seg<TG, LC>(src, acc);
+      if (CHUNK && ct == G - 1) {
+        // chunk done: publish its partial; the last chunk of the row finishes it
+        reduce_groups<LC>(acc, L.CG);
+        const int64_t row = t.row0;
+        const int p = t.a;
+        const int slot0 = a.poff[row], np = a.poff[row + 1] - slot0;
+        if (g == 0) {
+          float4* dst = reinterpret_cast<float4*>(a.part + (int64_t)(slot0 + p) * a.B + L.cg * LC);
+#pragma unroll
+          for (int i = 0; i < LC / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+        }
+        __threadfence();
+        __syncwarp();
+        int old = 0;
+        if (L.lane == 0) old = atomicAdd(&a.cnt[row], 1);
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old == np - 1) {
+          __threadfence();
+          float tot[LC];
+#pragma unroll
+          for (int i = 0; i < LC; ++i) tot[i] = 0.f;
+          for (int i = g; i < np; i += EG) {
+            const float4* ps_ = reinterpret_cast<const float4*>(a.part + (int64_t)(slot0 + i) * a.B + L.cg * LC);
+#pragma unroll
+            for (int q = 0; q < LC / 4; ++q) {
+              const float4 x = __ldcg(ps_ + q);
+              tot[4 * q] += x.x; tot[4 * q + 1] += x.y; tot[4 * q + 2] += x.z; tot[4 * q + 3] += x.w;
+            }
+          }
+          reduce_groups<LC>(tot, L.CG);
+          if (L.lane == 0) a.cnt[row] = 0;
+          if (g == 0) {
+#pragma unroll
+            for (int h = 0; h < LC / 8; ++h) {
+              const V8 pv = Store<TP>::load(a.qprev, row, a.B, L.cg * (LC / 8) + h);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) prev[8 * h + i] = pv.x[i];
+            }
+            const float4* yrow = reinterpret_cast<const float4*>(a.y + row * a.B + L.cg * LC);
+#pragma unroll
+            for (int i = 0; i < LC / 4; ++i) {
+              const float4 x = yrow[i];
+              yv[4 * i] = x.x; yv[4 * i + 1] = x.y; yv[4 * i + 2] = x.z; yv[4 * i + 3] = x.w;
+            }
+            update_seg<TO, LC>(L, row, (float)a.ldeg[row], tot, prev, yv, nrm);
+          }
+        }
+      }
+    } else if (!CHUNK) {
+      if (ct < G + OP) {
+        if (g == 0) put_prev<TP, LC, C::PW>(prev, ct - G, src);
+      } else {
+        if (g == 0) put_f32<LC, C::PW>(yv, ct - G - OP, src);
+        if (ct == rpr - 1) {
+          reduce_groups<LC>(acc, L.CG);
+          if (g == 0) update_seg<TO, LC>(L, t.row0 + cs, (float)d, acc, prev, yv, nrm);
+#pragma unroll
+          for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+        }
+      }
+    }
+    if (++ct == rpr) {
+      ct = 0;
+      ++cs;
+    }
+    issue((rc + S - 1) & (S - 1));
+    bcommit();
+  }
+}
+
+// One fused SpMM pass (see the top of this file).  Per warp, a ring of S
+// rounds of cp.async copies in shared memory keeps S row segments per lane in
+// flight: round i of a tile is issued S - 1 rounds before it is consumed.  A
+// lane group's round copies either one gathered neighbour row segment of
+// Q_k, or one piece of its own row's Q_{k-1} and y (fetched through the same
+// ring, after the row's gathers, so the update finds them on chip).
+template <typename TG, typename TP, typename TO, int LC>
+__global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __grid_constant__ SpmmArgs a) {
+  using C = Geo<TG, TP, TO, LC>;
   extern __shared__ __align__(16) unsigned char s_raw[];
   ColState* s_col = reinterpret_cast<ColState*>(s_raw);
   float* s_norm = reinterpret_cast<float*>(s_raw + sizeof(ColState) * a.B);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* ring = s_raw + kHeaderBytes + (size_t)warp * 32 * kRingLaneBytes;
+  int* s_ci = reinterpret_cast<int*>(s_raw + kHeaderBytes + (size_t)kBatchWarps * 32 * kRingLaneBytes) +
+              warp * 2 * kBTileSpan;
   for (int j = threadIdx.x; j < a.B; j += blockDim.x) {
     s_col[j] = a.col[j];
     s_norm[j] = 0.f;
   }
   __syncthreads();
-  const RP* rp = (const RP*)a.rp;
-  const int lane = threadIdx.x & 31;
-  const int CG = a.B / 8, EG = 32 / CG;
-  const int cg = lane % CG, g = lane / CG;
-  float nrm[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < a.nunits; w += nwarps) {
-    const int2 unit = a.units[w];
-    const int64_t row = unit.x;
-    const int64_t beg = rp[row], end = rp[row + 1];
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (unit.y < 0) {
-      RowOwn own{};
-      if (g == 0) own = load_own<TP>(a, row, cg);  // in flight during the gathers
-      gather_rows<TG, RP>(a, beg, end, g, EG, cg, acc);
-      reduce_groups(acc, CG);
-      if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, acc, own, nrm);
-    } else {
-      const int p = unit.y;
-      const int64_t lo = beg + (int64_t)p * kChunk, hi = min(lo + (int64_t)kChunk, end);
-      gather_rows<TG, RP>(a, lo, hi, g, EG, cg, acc);
-      reduce_groups(acc, CG);
-      const int slot0 = a.poff[row], np = a.poff[row + 1] - slot0;
-      if (g == 0) {
-        float* dst = a.part + (int64_t)(slot0 + p) * a.B + cg * 8;
-        *reinterpret_cast<float4*>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
-      }
-      __threadfence();
-      __syncwarp();
-      int old = 0;
-      if (lane == 0) old = atomicAdd(&a.cnt[row], 1);
-      old = __shfl_sync(0xffffffffu, old, 0);
-      if (old == np - 1) {
-        // last chunk of the row: add the partials in chunk order, then update
-        __threadfence();
-        float tot[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int i = g; i < np; i += EG) {
-          const float* src = a.part + (int64_t)(slot0 + i) * a.B + cg * 8;
-          const float4 p0 = __ldcg(reinterpret_cast<const float4*>(src));
-          const float4 p1 = __ldcg(reinterpret_cast<const float4*>(src + 4));
-          tot[0] += p0.x; tot[1] += p0.y; tot[2] += p0.z; tot[3] += p0.w;
-          tot[4] += p1.x; tot[5] += p1.y; tot[6] += p1.z; tot[7] += p1.w;
-        }
-        reduce_groups(tot, CG);
-        if (lane == 0) a.cnt[row] = 0;
-        if (g == 0) update_row<TP, TO>(a, s_col, row, (float)(end - beg), cg, tot, load_own<TP>(a, row, cg), nrm);
-      }
-    }
-  }
-  if (g == 0) {
+  Lane L;
+  L.a = &a;
+  L.s_col = s_col;
+  L.CG = a.B / LC;
+  L.EG = 32 / L.CG;
+  L.cg = lane % L.CG;
+  L.g = lane / L.CG;
+  L.lane = lane;
+  L.pol_keep = bpolicy_evict_last();
+  L.pol_stream = bpolicy_evict_first();
+  L.ring = (uint32_t)__cvta_generic_to_shared(ring) + lane * C::SB;
+  L.ring_p = ring + lane * C::SB;
+  L.qcur = static_cast<const unsigned char*>(a.qcur);
+  L.zero = static_cast<const unsigned char*>(a.zero) + L.cg * C::SB;
+  L.rowG = (size_t)a.B * C::sG;
+  L.rowP = (size_t)a.B * C::sP;
+  L.segG = (size_t)L.cg * C::SB;
+  L.segP = (size_t)L.cg * LC * C::sP;
+  float nrm[LC];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (nrm[i] != 0.f) atomicAdd(&s_norm[cg * 8 + i], nrm[i]);
+  for (int i = 0; i < LC; ++i) nrm[i] = 0.f;
+
+  const int64_t nwarps = (int64_t)gridDim.x * kBatchWarps;
+  int64_t w = (int64_t)blockIdx.x * kBatchWarps + warp;
+  int4 cur = make_int4(0, 0, 0, 0), nd = make_int4(0, 0, 0, 0);
+  if (w < a.ntiles) {
+    cur = a.tiles[w];
+    const BTile t0 = decode_btile(cur);
+    stage_indices(s_ci, a.ci, t0.e0, tile_len(t0), lane, L.pol_stream);
+    bcommit();
+    bwait<0>();
+    if (w + nwarps < a.ntiles) nd = a.tiles[w + nwarps];
   }
+  for (int buf = 0; w < a.ntiles; w += nwarps, buf ^= 1) {
+    __syncwarp();  // this tile's staged indices are visible; the other buffer is free
+    const BTile t = decode_btile(cur);
+    const int* ci_t = s_ci + buf * kBTileSpan + (int)(t.e0 & 3);
+    if (w + nwarps < a.ntiles) {  // the next tile's indices join this tile's first copy group
+      const BTile tn = decode_btile(nd);
+      stage_indices(s_ci + (buf ^ 1) * kBTileSpan, a.ci, tn.e0, tile_len(tn), lane, L.pol_stream);
+    }
+    int4 nd2 = make_int4(0, 0, 0, 0);
+    if (w + 2 * nwarps < a.ntiles) nd2 = a.tiles[w + 2 * nwarps];
+    if (t.kind == 0)
+      tile_rows_per_group<TG, TP, TO, LC>(L, t, ci_t, nrm);
+    else if (t.kind == 1)
+      tile_rows_per_warp<TG, TP, TO, LC, false>(L, t, ci_t, nrm);
+    else
+      tile_rows_per_warp<TG, TP, TO, LC, true>(L, t, ci_t, nrm);
+    cur = nd;
+    nd = nd2;
+    bwait<0>();  // only empty groups remain; the next tile restarts the ring at slot 0
+  }
+#pragma unroll
+  for (int i = 0; i < LC; ++i)
+    if (nrm[i] != 0.f) atomicAdd(&s_norm[L.cg * LC + i], nrm[i]);
   __syncthreads();
   for (int j = threadIdx.x; j < a.B; j += blockDim.x)
     if (s_norm[j] != 0.f) atomicAdd(&a.norm[j], s_norm[j]);
@@ -448,21 +774,34 @@ int device_sms() {
   return sms > 0 ? sms : 1;
 }
 
-template <typename RP, typename TG, typename TP, typename TO>
-void launch_spmm(const SpmmArgs& a, cudaStream_t st) {
-  const size_t smem = (sizeof(ColState) + sizeof(float)) * a.B;
-  const int grid = device_sms() * (2048 / kBatchThreads);
-  spmm_step_kernel<RP, TG, TP, TO><<<grid, kBatchThreads, smem, st>>>(a);
+template <typename TG, typename TP, typename TO, int LC>
+void launch_spmm_lc(const SpmmArgs& a, cudaStream_t st) {
+  static const cudaError_t attr = cudaFuncSetAttribute(spmm_step_kernel<TG, TP, TO, LC>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmSmem);
+  GP_CUDA_TRY(attr);
+  spmm_step_kernel<TG, TP, TO, LC><<<device_sms(), kBatchThreads, kSpmmSmem, st>>>(a);
   GP_LAUNCHED();
 }
 
-template <typename RP, typename H>
+// 16-bit gathers: a lane owns 16 columns (32 bytes per round) when B >= 16.
+template <typename TG, typename TP, typename TO>
+void launch_spmm(const SpmmArgs& a, cudaStream_t st) {
+  if constexpr (sizeof(TG) == 2) {
+    if (a.B >= 16) {
+      launch_spmm_lc<TG, TP, TO, 16>(a, st);
+      return;
+    }
+  }
+  launch_spmm_lc<TG, TP, TO, 8>(a, st);
+}
+
+template <typename H>
 void launch_stage(const SpmmArgs& a, int stage, cudaStream_t st) {
   switch (stage) {
-    case 0: launch_spmm<RP, float, float, float>(a, st); break;  // FP32
-    case 1: launch_spmm<RP, float, float, H>(a, st); break;      // first 16-bit write
-    case 2: launch_spmm<RP, H, float, H>(a, st); break;          // first 16-bit gather
-    default: launch_spmm<RP, H, H, H>(a, st); break;             // 16-bit
+    case 0: launch_spmm<float, float, float>(a, st); break;  // FP32
+    case 1: launch_spmm<float, float, H>(a, st); break;      // first 16-bit write
+    case 2: launch_spmm<H, float, H>(a, st); break;          // first 16-bit gather
+    default: launch_spmm<H, H, H>(a, st); break;             // 16-bit
   }
 }
 
@@ -493,28 +832,51 @@ ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st)
     norm_ = (float*)A.get(sizeof(float) * B);
     scratch_ = (int*)A.get(sizeof(int) * 4 * B + sizeof(int64_t) * B + sizeof(float) * 2 * B + 16);
     outs_ = A.get(sizeof(void*) * B);
-    // long-row chunk table for kChunk-entry chunks
+    // tiles of the pass: chunks of the long rows, then runs of equal-degree rows
     const std::vector<int64_t>& rp = g.h_rp_relabelled;
-    std::vector<int2> units;
+    const int EG = 32 / (B / 8);
+    std::vector<int4> tiles;
     std::vector<int> poff(1, 0);
+    std::vector<int64_t> ldeg;
     int64_t row = 0;
-    while (row < g.n_active && rp[row + 1] - rp[row] > kChunk) {
-      const int64_t np = (rp[row + 1] - rp[row] + kChunk - 1) / kChunk;
-      for (int64_t p = 0; p < np; ++p) units.push_back(make_int2((int)row, (int)p));
+    while (row < g.n_active && rp[row + 1] - rp[row] > kBTileCap) {
+      const int64_t deg = rp[row + 1] - rp[row];
+      const int64_t np = (deg + kBTileCap - 1) / kBTileCap;
+      if (np > 0x7fff) throw Error{GP_EINVAL, "a row has too many entries for the batched schedule"};
+      for (int64_t p = 0; p < np; ++p)
+        tiles.push_back(make_btile(row, rp[row] + p * kBTileCap, 2, (int)p,
+                                   (int)std::min<int64_t>(kBTileCap, deg - p * kBTileCap)));
       poff.push_back(poff.back() + (int)np);
+      ldeg.push_back(deg);
       ++row;
     }
     nlong_ = (int)row;
-    for (; row < g.n_active; ++row) units.push_back(make_int2((int)row, -1));
-    nunits_ = (int64_t)units.size();
-    units_ = (int2*)A.get(sizeof(int2) * std::max<size_t>(units.size(), 1));
+    while (row < g.n_active) {
+      const int64_t d = rp[row + 1] - rp[row];
+      int64_t run = row + 1;
+      while (run < g.n_active && rp[run + 1] - rp[run] == d) ++run;
+      int64_t cap = std::max<int64_t>(1, std::min<int64_t>(kBTileCost / (d + 3), kBTileCap / d));
+      if (cap >= EG) cap -= cap % EG;  // whole rounds of the lane groups
+      for (; row < run;) {
+        const int64_t nr = std::min(cap, run - row);
+        tiles.push_back(make_btile(row, rp[row], nr >= EG ? 0 : 1, (int)nr, (int)d));
+        row += nr;
+      }
+    }
+    ntiles_ = (int64_t)tiles.size();
+    tiles_ = (int4*)A.get(sizeof(int4) * std::max<size_t>(tiles.size(), 1));
     poff_ = (int*)A.get(sizeof(int) * poff.size());
+    ldeg_ = (int64_t*)A.get(sizeof(int64_t) * std::max<size_t>(ldeg.size(), 1));
     part_ = (float*)A.get(sizeof(float) * (size_t)std::max(poff.back(), 1) * B);
     cnt_ = (int*)A.get(sizeof(int) * std::max(nlong_, 1));
-    if (!units.empty())
-      GP_CUDA_TRY(cudaMemcpyAsync(units_, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, st_));
+    zero_ = A.get(sizeof(float) * B);
+    if (!tiles.empty())
+      GP_CUDA_TRY(cudaMemcpyAsync(tiles_, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, st_));
     GP_CUDA_TRY(cudaMemcpyAsync(poff_, poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice, st_));
+    if (!ldeg.empty())
+      GP_CUDA_TRY(cudaMemcpyAsync(ldeg_, ldeg.data(), sizeof(int64_t) * ldeg.size(), cudaMemcpyHostToDevice, st_));
     GP_CUDA_TRY(cudaMemsetAsync(cnt_, 0, sizeof(int) * std::max(nlong_, 1), st_));
+    GP_CUDA_TRY(cudaMemsetAsync(zero_, 0, sizeof(float) * B, st_));
     GP_CUDA_TRY(cudaMemsetAsync(col_, 0, sizeof(ColState) * B, st_));
     GP_CUDA_TRY(cudaMemsetAsync(par_, 0, sizeof(ColParam) * B, st_));
     GP_CUDA_TRY(cudaMemsetAsync(stat_, 0, sizeof(ColStat) * B, st_));
@@ -533,8 +895,8 @@ void ColumnEngine::release() {
   if (st_) cudaStreamSynchronize(st_);
   Allocator& A = g_.alloc;
   for (void* p : {(void*)f_[0], (void*)f_[1], h_[0], h_[1], (void*)y_, (void*)col_, (void*)par_, (void*)stat_,
-                  (void*)norm_, (void*)scratch_, outs_, stage_, (void*)units_, (void*)poff_, (void*)part_,
-                  (void*)cnt_})
+                  (void*)norm_, (void*)scratch_, outs_, stage_, (void*)tiles_, (void*)poff_, (void*)ldeg_,
+                  (void*)part_, (void*)cnt_, zero_})
     A.put(p);
   stat_ = nullptr;
   stage_ = nullptr;
@@ -546,7 +908,9 @@ void ColumnEngine::release() {
   norm_ = nullptr;
   scratch_ = nullptr;
   outs_ = nullptr;
-  units_ = nullptr;
+  tiles_ = nullptr;
+  ldeg_ = nullptr;
+  zero_ = nullptr;
   poff_ = nullptr;
   part_ = nullptr;
   cnt_ = nullptr;
@@ -667,9 +1031,8 @@ void ColumnEngine::pass() {
     if (h_pass_ >= 0) stage = std::min(3, pass_ - h_pass_ + 1);
   }
   SpmmArgs a;
-  a.units = units_;
-  a.nunits = nunits_;
-  a.rp = g_.rp;
+  a.tiles = tiles_;
+  a.ntiles = ntiles_;
   a.ci = g_.ci;
   const int cur = pass_ & 1, nxt = (pass_ + 1) & 1;
   a.qcur = stage >= 2 ? h_[cur] : (const void*)f_[cur];
@@ -679,17 +1042,14 @@ void ColumnEngine::pass() {
   a.col = col_;
   a.norm = norm_;
   a.poff = poff_;
+  a.ldeg = ldeg_;
   a.part = part_;
   a.cnt = cnt_;
+  a.zero = zero_;
   a.na = g_.n_active;
   a.B = B_;
-  if (g_.rp64) {
-    if (storage_ == GP_F16) launch_stage<int64_t, __half>(a, stage, st_);
-    else launch_stage<int64_t, __nv_bfloat16>(a, stage, st_);
-  } else {
-    if (storage_ == GP_F16) launch_stage<int32_t, __half>(a, stage, st_);
-    else launch_stage<int32_t, __nv_bfloat16>(a, stage, st_);
-  }
+  if (storage_ == GP_F16) launch_stage<__half>(a, stage, st_);
+  else launch_stage<__nv_bfloat16>(a, stage, st_);
   ++pass_;
   ++passes_total_;
 }

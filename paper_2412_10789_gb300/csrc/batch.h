@@ -102,10 +102,12 @@ class ColumnEngine {
   int* scratch_ = nullptr;
   void* outs_ = nullptr;
   void* stage_ = nullptr;
-  int2* units_ = nullptr;
-  int64_t nunits_ = 0;
+  int4* tiles_ = nullptr;     // schedule of the pass (batch.cu)
+  int64_t ntiles_ = 0;
   int nlong_ = 0;
   int* poff_ = nullptr;
+  int64_t* ldeg_ = nullptr;   // degrees of the long (chunked) rows
+  void* zero_ = nullptr;      // B zero floats
   float* part_ = nullptr;
   int* cnt_ = nullptr;
   std::vector<Slot> slots_;
