@@ -56,15 +56,25 @@ def parse():
     p.add_argument("--power-baseline", action="store_true", help="also time the GPU PwMethod")
     p.add_argument("--no-batched", action="store_true", help="skip the batched and served forms")
     p.add_argument("--batch-width", type=int, default=128)
+    p.add_argument("--forms", default="single,batched,serving",
+                   help="comma list of the forms to time (the single-source form is always run)")
+    p.add_argument("--batch-storage", default="bf16,fp32", help="storages of the batched form")
+    p.add_argument("--batch-reps", type=int, default=3)
     return p.parse_args()
 
 
-def bench_batched(gp, dg_single, g, queries, dev, world, reps=3):
-    """gp_batch over the step's queries as one block: BF16 storage (FP32 warm-up)
-    at l1 <= 1e-4, and FP32 storage at l1 <= 1e-6; queries/s over `reps` runs."""
+BATCH_FORMS = {"bf16": ("bf16_tol1e-4", "GP_BF16", 1e-4), "fp16": ("fp16_tol1e-4", "GP_F16", 1e-4),
+               "fp32": ("fp32_tol1e-6", "GP_F32", 1e-6), "fp32_1e-4": ("fp32_tol1e-4", "GP_F32", 1e-4)}
+
+
+def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32"), reps=3):
+    """gp_batch over the step's queries as one block: BF16/FP16 storage (FP32
+    warm-up) at l1 <= 1e-4, FP32 storage at l1 <= 1e-6; queries/s over `reps` runs."""
     import torch
     res = {}
-    for name, storage, tol in (("bf16_tol1e-4", gp.GP_BF16, 1e-4), ("fp32_tol1e-6", gp.GP_F32, 1e-6)):
+    for key in storages:
+        name, storage_name, tol = BATCH_FORMS[key]
+        storage = getattr(gp, storage_name)
         dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=storage,
                                 block_width=min(256, len(queries)))
         ys = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in queries]
@@ -375,8 +385,12 @@ def run_ours(args, rank, world):
         dt = time.perf_counter() - t0
         power = {"value": len(queries) / dt, "unit": UNIT, "what": "Algorithm 1 on the same GPU, same queries"}
     # ---- batched and served forms on the same graph and queries
-    batched = None if args.no_batched else bench_batched(gp, dg, g, queries, dev, world)
-    serving = None if args.no_batched else bench_serving(gp, g, queries, dev, world)
+    forms = set(args.forms.split(","))
+    batched = None
+    if not args.no_batched and "batched" in forms:
+        batched = bench_batched(gp, dg, g, queries, dev, world, storages=args.batch_storage.split(","),
+                                reps=args.batch_reps)
+    serving = None if args.no_batched or "serving" not in forms else bench_serving(gp, g, queries, dev, world)
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -125,6 +125,8 @@ struct Store;
 template <>
 struct Store<float> {
   static constexpr int bytes = 4;
+  template <int N>
+  __device__ static __forceinline__ void finish(float*) {}  // sums are in Q units
   struct Raw {
     float4 a, b;
   };
@@ -150,22 +152,18 @@ struct Store<float> {
 template <>
 struct Store<__nv_bfloat16> {
   static constexpr int bytes = 2;
+  template <int N>
+  __device__ static __forceinline__ void finish(float*) {}  // sums are in Q units
   using Raw = uint4;
   __device__ static __forceinline__ Raw lds(const unsigned char* p) { return *reinterpret_cast<const uint4*>(p); }
-  // Widen each bf16 pair to two floats (a shift and a mask) and add them to
-  // the accumulator pair with one packed FP32 add.
+  // acc += each bf16 value, widened exactly inside a mixed-precision FP32 add.
   __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const unsigned long long v =
-          ((unsigned long long)(u[i] & 0xffff0000u) << 32) | (unsigned long long)(u[i] << 16);
-      unsigned long long s =
-          ((unsigned long long)__float_as_uint(acc[2 * i + 1]) << 32) | __float_as_uint(acc[2 * i]);
-      asm("add.rn.f32x2 %0, %0, %1;" : "+l"(s) : "l"(v));
-      acc[2 * i] = __uint_as_float((uint32_t)s);
-      acc[2 * i + 1] = __uint_as_float((uint32_t)(s >> 32));
-    }
+    for (int i = 0; i < 4; ++i)
+      asm("{ .reg .b16 lo, hi; mov.b32 {lo, hi}, %2; add.rn.f32.bf16 %0, lo, %0; add.rn.f32.bf16 %1, hi, %1; }"
+          : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+          : "r"(u[i]));
   }
   __device__ static __forceinline__ void decode(const Raw& w, float v[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
@@ -196,14 +194,20 @@ struct Store<__half> {
   static constexpr int bytes = 2;
   using Raw = uint4;
   __device__ static __forceinline__ Raw lds(const unsigned char* p) { return *reinterpret_cast<const uint4*>(p); }
+  // acc += each stored value (Q * 2^12), widened exactly inside a
+  // mixed-precision FP32 add; finish() removes the 2^12 once per row.
   __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[i]));
-      acc[2 * i] = fmaf(f.x, 1.0f / kF16Scale, acc[2 * i]);
-      acc[2 * i + 1] = fmaf(f.y, 1.0f / kF16Scale, acc[2 * i + 1]);
-    }
+    for (int i = 0; i < 4; ++i)
+      asm("{ .reg .b16 lo, hi; mov.b32 {lo, hi}, %2; add.rn.f32.f16 %0, lo, %0; add.rn.f32.f16 %1, hi, %1; }"
+          : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+          : "r"(u[i]));
+  }
+  template <int N>
+  __device__ static __forceinline__ void finish(float acc[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] *= 1.0f / kF16Scale;  // exact: a power of two
   }
   __device__ static __forceinline__ void decode(const Raw& w, float v[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
@@ -267,94 +271,48 @@ struct Geo {
   static constexpr int S = kRingLaneBytes / SB;   // rounds in flight
   static constexpr int OP = LC * sP / SB;         // rounds of the own Q_{k-1} segment (1 or 2)
   static constexpr int OY = LC * 4 / SB;          // rounds of the own y segment (1 or 2)
+  static constexpr int OWN = OP + OY;
   static constexpr int PW = SB / 4;               // floats per round of an FP32 segment
+  static constexpr uint32_t kStride = 32 * SB;    // ring bytes per round (whole warp)
+  static constexpr uint32_t kMask = S * kStride - 1;
   static_assert(S >= 2 && (S & (S - 1)) == 0, "ring depth must be a power of two");
-  static_assert(SB == 16 || SB == 32, "a round moves 16 or 32 bytes per lane");
+  static_assert(SB == 16 || SB == 32 || SB == 64, "a round moves 16, 32 or 64 bytes per lane");
 };
 
 // Per-lane constants of the pass.
 struct Lane {
   const SpmmArgs* a;
   const ColState* s_col;
-  uint32_t ring;               // shared address of this lane's slot 0
-  const unsigned char* ring_p; // the same, generic
-  const unsigned char* qcur;   // Q_k
-  const unsigned char* zero;   // zero segment
-  size_t rowG, rowP, segG, segP;
+  uint32_t ring;                // shared address of this lane's slot 0
+  const unsigned char* ring_p;  // the same, generic
+  const unsigned char* qseg;    // Q_k + this lane's segment offset
+  const unsigned char* pseg;    // Q_{k-1} + this lane's segment offset
+  const unsigned char* yseg;    // y + this lane's segment offset
+  const unsigned char* zero;    // zero segment
+  uint32_t rowG;                // bytes of a Q_k row
+  size_t rowP, rowY;            // bytes of a Q_{k-1} row, of a y row
   uint64_t pol_keep, pol_stream;
   int cg, g, CG, EG, lane;
 };
+
+// Source of the gathered segment of neighbour v (rows beyond the active ones,
+// which only an unvalidated asymmetric CSR can list, read zeros).
+__device__ __forceinline__ const unsigned char* gather_src(const Lane& L, int v) {
+  return v < L.a->na ? L.qseg + (uint64_t)(uint32_t)v * L.rowG : L.zero;
+}
+
+// Source of piece o (SB bytes) of row u's own Q_{k-1} segment (o < OP) or y
+// segment.
+template <int SB, int OP>
+__device__ __forceinline__ const unsigned char* own_src(const Lane& L, int64_t u, int o) {
+  return o < OP ? L.pseg + (size_t)u * L.rowP + (size_t)o * SB : L.yseg + (size_t)u * L.rowY + (size_t)(o - OP) * SB;
+}
 
 // Add one gathered segment (LC values of TG) from a ring slot.
 template <typename TG, int LC>
 __device__ __forceinline__ void add_seg(const unsigned char* p, float acc[LC]) {
 #pragma unroll
   for (int h = 0; h < LC / 8; ++h) Store<TG>::add(Store<TG>::lds(p + h * 8 * Store<TG>::bytes), acc + 8 * h);
-}
-
-// Piece o of an LC-float segment (PW floats per piece) from a ring slot.
-template <int LC, int PW>
-__device__ __forceinline__ void put_f32(float v[LC], int o, const unsigned char* src) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  if constexpr (PW == LC) {
-#pragma unroll
-    for (int i = 0; i < LC / 4; ++i) {
-      const float4 x = s4[i];
-      v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
-    }
-  } else {
-    static_assert(2 * PW == LC, "one or two pieces per segment");
-#pragma unroll
-    for (int i = 0; i < PW / 4; ++i) {
-      const float4 x = s4[i];
-      if (o == 0) {
-        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
-      } else {
-        v[PW + 4 * i] = x.x; v[PW + 4 * i + 1] = x.y; v[PW + 4 * i + 2] = x.z; v[PW + 4 * i + 3] = x.w;
-      }
-    }
-  }
-}
-
-// Piece o of the own Q_{k-1} segment.
-template <typename TP, int LC, int PW>
-__device__ __forceinline__ void put_prev(float prev[LC], int o, const unsigned char* src) {
-  if constexpr (Store<TP>::bytes == 4) {
-    put_f32<LC, PW>(prev, o, src);
-  } else {  // a 16-bit segment always fits one round
-#pragma unroll
-    for (int h = 0; h < LC / 8; ++h) Store<TP>::decode(Store<TP>::lds(src + 16 * h), prev + 8 * h);
-  }
-}
-
-// Row u's update from its neighbour sums acc, Q_{k-1}(u) (prev) and y(u) for
-// this lane's LC columns: r = 2 acc - d prev, Q_{k+1} = r / d, y += c r.
-// Retired columns keep their values (y final; Q copied).
-template <typename TO, int LC>
-__device__ __forceinline__ void update_seg(const Lane& L, int64_t u, float d, const float acc[LC],
-                                           const float prev[LC], float yv[LC], float nrm[LC]) {
-  const SpmmArgs& a = *L.a;
-  const float inv = 1.0f / d;
-#pragma unroll
-  for (int h = 0; h < LC / 8; ++h) {
-    V8 out;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int c = 8 * h + i;
-      const ColState& cs = L.s_col[L.cg * LC + c];
-      out.x[i] = prev[c];
-      if (cs.active) {
-        const float r = 2.0f * acc[c] - d * prev[c];
-        out.x[i] = r * inv;
-        yv[c] = fmaf(cs.coef, r, yv[c]);
-        nrm[c] += fabsf(r);
-      }
-    }
-    Store<TO>::store(a.qnext, u, a.B, L.cg * (LC / 8) + h, out);
-  }
-  float4* yrow = reinterpret_cast<float4*>(a.y + u * a.B + L.cg * LC);
-#pragma unroll
-  for (int i = 0; i < LC / 4; ++i) yrow[i] = make_float4(yv[4 * i], yv[4 * i + 1], yv[4 * i + 2], yv[4 * i + 3]);
 }
 
 // Copy a tile's col_idx entries [e0, e0 + len) into a warp's staging buffer
@@ -370,10 +328,109 @@ __device__ __forceinline__ void stage_indices(int* buf, const int32_t* ci, int64
 
 __device__ __forceinline__ int tile_len(const BTile& t) { return t.kind == 2 ? t.b : t.a * t.b; }
 
+// SB bytes from global to shared memory in 16-byte cp.async copies.
 template <int SB>
 __device__ __forceinline__ void cp_seg(uint32_t dst, const unsigned char* src, uint64_t pol) {
+  if constexpr (SB == 16) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
+                 : "memory");
+  } else if constexpr (SB == 32) {
+    asm volatile(
+        "cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n\t"
+        "cp.async.cg.shared.global.L2::cache_hint [%0+16], [%1+16], 16, %2;" ::"r"(dst),
+        "l"(src), "l"(pol)
+        : "memory");
+  } else {
+    asm volatile(
+        "cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n\t"
+        "cp.async.cg.shared.global.L2::cache_hint [%0+16], [%1+16], 16, %2;\n\t"
+        "cp.async.cg.shared.global.L2::cache_hint [%0+32], [%1+32], 16, %2;\n\t"
+        "cp.async.cg.shared.global.L2::cache_hint [%0+48], [%1+48], 16, %2;" ::"r"(dst),
+        "l"(src), "l"(pol)
+        : "memory");
+  }
+}
+
+// The row update, applied as row u's own segments land (after its gathers,
+// so acc holds the final neighbour sums).  A Q_{k-1} piece (columns C0 ..
+// C0 + PC - 1) turns acc into r = 2 acc - d Q_{k-1} and writes
+// Q_{k+1} = r / d; a y piece (columns C0 .. C0 + PW - 1) adds c r to y.
+// Retired columns keep their values (Q copied, y final).
+template <typename TP, typename TO, int LC, int PC, int C0>
+__device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, const unsigned char* src, float acc[LC],
+                                           float nrm[LC]) {
+  float prev[PC];
+  if constexpr (Store<TP>::bytes == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-  for (int h = 0; h < SB / 16; ++h) bcp16(dst + 16 * h, src + 16 * h, pol);
+    for (int q = 0; q < PC / 4; ++q) {
+      const float4 x = s4[q];
+      prev[4 * q] = x.x; prev[4 * q + 1] = x.y; prev[4 * q + 2] = x.z; prev[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int h = 0; h < PC / 8; ++h) Store<TP>::decode(Store<TP>::lds(src + 16 * h), prev + 8 * h);
+  }
+  const float inv = 1.0f / d;
+#pragma unroll
+  for (int h = 0; h < PC / 8; ++h) {
+    V8 out;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = C0 + 8 * h + i;
+      const ColState cs = L.s_col[L.cg * LC + c];
+      const float p = prev[8 * h + i];
+      const float r = 2.0f * acc[c] - d * p;
+      out.x[i] = cs.active ? r * inv : p;
+      acc[c] = cs.active ? r : 0.f;
+      nrm[c] += fabsf(acc[c]);
+    }
+    Store<TO>::store(L.a->qnext, u, L.a->B, L.cg * (LC / 8) + C0 / 8 + h, out);
+  }
+}
+
+template <int LC, int PW, int C0>
+__device__ __forceinline__ void y_piece(const Lane& L, int64_t u, const unsigned char* src, const float acc[LC]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* yrow = reinterpret_cast<float4*>(L.a->y + u * L.a->B + L.cg * LC + C0);
+#pragma unroll
+  for (int q = 0; q < PW / 4; ++q) {
+    float4 x = s4[q];
+    float* xv = reinterpret_cast<float*>(&x);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = C0 + 4 * q + k;
+      const ColState cs = L.s_col[L.cg * LC + c];
+      xv[k] = fmaf(cs.active ? cs.coef : 0.f, acc[c], xv[k]);
+    }
+    yrow[q] = x;
+  }
+}
+
+// Own round o of row u: Q_{k-1} pieces (o < OP), then y pieces.
+template <typename TP, typename TO, int LC, int SB, int OP, int OY>
+__device__ __forceinline__ void own_round(const Lane& L, int64_t u, float d, int o, const unsigned char* src,
+                                          float acc[LC], float nrm[LC]) {
+  constexpr int PC = LC / OP, PW = LC / OY;
+  if (o < OP) {
+    if constexpr (OP == 1) {
+      prev_piece<TP, TO, LC, PC, 0>(L, u, d, src, acc, nrm);
+    } else {
+      if (o == 0)
+        prev_piece<TP, TO, LC, PC, 0>(L, u, d, src, acc, nrm);
+      else
+        prev_piece<TP, TO, LC, PC, PC>(L, u, d, src, acc, nrm);
+    }
+  } else {
+    if constexpr (OY == 1) {
+      y_piece<LC, PW, 0>(L, u, src, acc);
+    } else {
+      if (o == OP)
+        y_piece<LC, PW, 0>(L, u, src, acc);
+      else
+        y_piece<LC, PW, PW>(L, u, src, acc);
+    }
+  }
 }
 
 // Kind 0 tile: lane group g takes rows g, g + EG, ... of the tile; a row is d
@@ -383,72 +440,118 @@ __device__ __forceinline__ void cp_seg(uint32_t dst, const unsigned char* src, u
 template <typename TG, typename TP, typename TO, int LC>
 __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
-  constexpr int S = C::S, SB = C::SB, OP = C::OP;
-  const SpmmArgs& a = *L.a;
+  constexpr int S = C::S, SB = C::SB, OP = C::OP, OWN = C::OWN;
   const int d = t.b, nrows = t.a, EG = L.EG;
-  const int rpr = d + C::OP + C::OY;
   const int nseq = (nrows + EG - 1) / EG;
-  const int R = nseq * rpr;
-  // producer: sequence ps, round pt, next index pj; consumer: sequence cs, round ct
-  int ps = 0, pt = 0, pj = L.g * d, prow = L.g;
-  int cs = 0, ct = 0, crow = L.g;
-  auto issue = [&](int slot) {
-    if (ps < nseq) {
-      if (prow < nrows) {
-        const uint32_t dst = L.ring + (uint32_t)(slot * 32 * SB);
-        if (pt < d) {
-          const int v = ci_t[pj];
-          cp_seg<SB>(dst, v < a.na ? L.qcur + (size_t)v * L.rowG + L.segG : L.zero, L.pol_keep);
-        } else {
-          const int64_t u = t.row0 + prow;
-          const int o = pt - d;
-          const unsigned char* src =
-              o < OP ? static_cast<const unsigned char*>(a.qprev) + (size_t)u * L.rowP + L.segP + (size_t)o * SB
-                     : reinterpret_cast<const unsigned char*>(a.y + u * a.B + L.cg * LC) + (size_t)(o - OP) * SB;
-          cp_seg<SB>(dst, src, L.pol_stream);
+  const int R = nseq * (d + OWN);
+  // producer: row sequence, gathers left in the row, own round, next index
+  int p_seq = 0, p_left = d, p_own = 0, p_row = L.g;
+  const int* p_ci = ci_t + L.g * d;
+  uint32_t p_off = 0;
+  auto issue = [&]() {
+    if (p_seq < nseq) {
+      const uint32_t dst = L.ring + p_off;
+      if (p_left > 0) {
+        if (p_row < nrows) cp_seg<SB>(dst, gather_src(L, *p_ci), L.pol_keep);
+        ++p_ci;
+        --p_left;
+      } else {
+        if (p_row < nrows) cp_seg<SB>(dst, own_src<SB, OP>(L, t.row0 + p_row, p_own), L.pol_stream);
+        if (++p_own == OWN) {
+          p_own = 0;
+          ++p_seq;
+          p_row += EG;
+          p_ci += (EG - 1) * d;
+          p_left = d;
         }
       }
-      ++pj;
-      if (++pt == rpr) {
-        pt = 0;
-        ++ps;
-        prow += EG;
-        pj = prow * d;
-      }
     }
+    p_off = (p_off + C::kStride) & C::kMask;
   };
-  float acc[LC], prev[LC], yv[LC];
+  float acc[LC];
 #pragma unroll
-  for (int i = 0; i < LC; ++i) acc[i] = prev[i] = yv[i] = 0.f;
+  for (int i = 0; i < LC; ++i) acc[i] = 0.f;
 #pragma unroll 1
   for (int i = 0; i < S - 1; ++i) {
-    issue(i);
+    issue();
     bcommit();
   }
+  int c_left = d, c_own = 0, c_row = L.g;
+  uint32_t c_off = 0;
 #pragma unroll 1
   for (int rc = 0; rc < R; ++rc) {
     bwait<S - 2>();  // round rc has landed
-    const unsigned char* src = L.ring_p + (rc & (S - 1)) * 32 * SB;
-    const bool mine = crow < nrows;
-    if (ct < d) {
+    const unsigned char* src = L.ring_p + c_off;
+    const bool mine = c_row < nrows;
+    if (c_left > 0) {
       if (mine) add_seg<TG, LC>(src, acc);
-    } else if (ct < d + OP) {
-      if (mine) put_prev<TP, LC, C::PW>(prev, ct - d, src);
+      --c_left;
     } else {
-      if (mine) put_f32<LC, C::PW>(yv, ct - d - OP, src);
-      if (ct == rpr - 1) {
-        if (mine) update_seg<TO, LC>(L, t.row0 + crow, (float)d, acc, prev, yv, nrm);
+      if (c_own == 0) Store<TG>::template finish<LC>(acc);
+      if (mine) own_round<TP, TO, LC, SB, OP, C::OY>(L, t.row0 + c_row, (float)d, c_own, src, acc, nrm);
+      if (++c_own == OWN) {
 #pragma unroll
         for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+        c_own = 0;
+        c_row += EG;
+        c_left = d;
       }
     }
-    if (++ct == rpr) {
-      ct = 0;
-      ++cs;
-      crow += EG;
-    }
-    issue((rc + S - 1) & (S - 1));
+    c_off = (c_off + C::kStride) & C::kMask;
+    issue();
     bcommit();
+  }
+}
+
+// Last chunk of a long row: add the chunk partials in chunk order and update
+// the row (its own segments are read directly: long rows are few).
+template <typename TP, typename TO, int LC>
+__device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int slot0, int np, float nrm[LC]) {
+  const SpmmArgs& a = *L.a;
+  __threadfence();
+  float tot[LC];
+#pragma unroll
+  for (int i = 0; i < LC; ++i) tot[i] = 0.f;
+  for (int i = L.g; i < np; i += L.EG) {
+    const float4* src = reinterpret_cast<const float4*>(a.part + (int64_t)(slot0 + i) * a.B + L.cg * LC);
+#pragma unroll
+    for (int q = 0; q < LC / 4; ++q) {
+      const float4 x = __ldcg(src + q);
+      tot[4 * q] += x.x; tot[4 * q + 1] += x.y; tot[4 * q + 2] += x.z; tot[4 * q + 3] += x.w;
+    }
+  }
+  reduce_groups<LC>(tot, L.CG);
+  if (L.lane == 0) a.cnt[row] = 0;
+  if (L.g == 0) {
+    const float d = (float)a.ldeg[row];
+    const float inv = 1.0f / d;
+#pragma unroll
+    for (int h = 0; h < LC / 8; ++h) {
+      const V8 pv = Store<TP>::load(a.qprev, row, a.B, L.cg * (LC / 8) + h);
+      V8 out;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int c = 8 * h + i;
+        const ColState cs = L.s_col[L.cg * LC + c];
+        const float r = 2.0f * tot[c] - d * pv.x[i];
+        out.x[i] = cs.active ? r * inv : pv.x[i];
+        tot[c] = cs.active ? r : 0.f;
+        nrm[c] += fabsf(tot[c]);
+      }
+      Store<TO>::store(a.qnext, row, a.B, L.cg * (LC / 8) + h, out);
+    }
+    float4* yrow = reinterpret_cast<float4*>(a.y + row * a.B + L.cg * LC);
+#pragma unroll
+    for (int q = 0; q < LC / 4; ++q) {
+      float4 x = yrow[q];
+      float* xv = reinterpret_cast<float*>(&x);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const ColState cs = L.s_col[L.cg * LC + 4 * q + k];
+        xv[k] = fmaf(cs.active ? cs.coef : 0.f, tot[4 * q + k], xv[k]);
+      }
+      yrow[q] = x;
+    }
   }
 }
 
@@ -459,62 +562,62 @@ __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& 
 template <typename TG, typename TP, typename TO, int LC, bool CHUNK>
 __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
-  constexpr int S = C::S, SB = C::SB, OP = C::OP;
+  constexpr int S = C::S, SB = C::SB, OP = C::OP, OWN = C::OWN;
   const SpmmArgs& a = *L.a;
   const int EG = L.EG, g = L.g;
   const int d = t.b;  // entries per row (kind 1) or of the chunk (kind 2)
   const int G = (d + EG - 1) / EG;
-  const int rpr = CHUNK ? G : G + C::OP + C::OY;
   const int nseq = CHUNK ? 1 : t.a;
-  const int R = nseq * rpr;
-  int ps = 0, pt = 0, pj = g;
-  int cs = 0, ct = 0;
-  auto issue = [&](int slot) {
-    if (ps < nseq) {
-      const uint32_t dst = L.ring + (uint32_t)(slot * 32 * SB);
-      if (pt < G) {
-        if (pt * EG + g < d) {
-          const int v = ci_t[pj];
-          cp_seg<SB>(dst, v < a.na ? L.qcur + (size_t)v * L.rowG + L.segG : L.zero, L.pol_keep);
+  const int R = nseq * (CHUNK ? G : G + OWN);
+  int p_seq = 0, p_left = G, p_own = 0, p_j = g;
+  const int* p_ci = ci_t + g;
+  uint32_t p_off = 0;
+  auto issue = [&]() {
+    if (p_seq < nseq) {
+      const uint32_t dst = L.ring + p_off;
+      if (p_left > 0) {
+        if (p_j < d) cp_seg<SB>(dst, gather_src(L, *p_ci), L.pol_keep);
+        p_ci += EG;
+        p_j += EG;
+        if (--p_left == 0 && CHUNK) ++p_seq;
+      } else {
+        if (g == 0) cp_seg<SB>(dst, own_src<SB, OP>(L, t.row0 + p_seq, p_own), L.pol_stream);
+        if (++p_own == OWN) {
+          p_own = 0;
+          ++p_seq;
+          p_left = G;
+          p_j = g;
+          p_ci = ci_t + p_seq * d + g;
         }
-        pj += EG;
-      } else if (!CHUNK && g == 0) {
-        const int64_t u = t.row0 + ps;
-        const int o = pt - G;
-        const unsigned char* src =
-            o < OP ? static_cast<const unsigned char*>(a.qprev) + (size_t)u * L.rowP + L.segP + (size_t)o * SB
-                   : reinterpret_cast<const unsigned char*>(a.y + u * a.B + L.cg * LC) + (size_t)(o - OP) * SB;
-        cp_seg<SB>(dst, src, L.pol_stream);
-      }
-      if (++pt == rpr) {
-        pt = 0;
-        ++ps;
-        pj = ps * d + g;
       }
     }
+    p_off = (p_off + C::kStride) & C::kMask;
   };
-  float acc[LC], prev[LC], yv[LC];
+  float acc[LC];
 #pragma unroll
-  for (int i = 0; i < LC; ++i) acc[i] = prev[i] = yv[i] = 0.f;
+  for (int i = 0; i < LC; ++i) acc[i] = 0.f;
 #pragma unroll 1
   for (int i = 0; i < S - 1; ++i) {
-    issue(i);
+    issue();
     bcommit();
   }
+  int c_seq = 0, c_left = G, c_own = 0, c_j = g;
+  uint32_t c_off = 0;
 #pragma unroll 1
   for (int rc = 0; rc < R; ++rc) {
     bwait<S - 2>();  // round rc has landed
-    const unsigned char* src = L.ring_p + (rc & (S - 1)) * 32 * SB;
-    if (ct < G) {
-      if (ct * EG + g < d) add_seg<TG, LC>(src, acc);
-      if (CHUNK && ct == G - 1) {
+    const unsigned char* src = L.ring_p + c_off;
+    if (c_left > 0) {
+      if (c_j < d) add_seg<TG, LC>(src, acc);
+      c_j += EG;
+      if (--c_left == 0 && CHUNK) {
         // chunk done: publish its partial; the last chunk of the row finishes it
         reduce_groups<LC>(acc, L.CG);
+        Store<TG>::template finish<LC>(acc);
         const int64_t row = t.row0;
-        const int p = t.a;
         const int slot0 = a.poff[row], np = a.poff[row + 1] - slot0;
         if (g == 0) {
-          float4* dst = reinterpret_cast<float4*>(a.part + (int64_t)(slot0 + p) * a.B + L.cg * LC);
+          float4* dst = reinterpret_cast<float4*>(a.part + (int64_t)(slot0 + t.a) * a.B + L.cg * LC);
 #pragma unroll
           for (int i = 0; i < LC / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
         }
@@ -523,56 +626,25 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
         int old = 0;
         if (L.lane == 0) old = atomicAdd(&a.cnt[row], 1);
         old = __shfl_sync(0xffffffffu, old, 0);
-        if (old == np - 1) {
-          __threadfence();
-          float tot[LC];
-#pragma unroll
-          for (int i = 0; i < LC; ++i) tot[i] = 0.f;
-          for (int i = g; i < np; i += EG) {
-            const float4* ps_ = reinterpret_cast<const float4*>(a.part + (int64_t)(slot0 + i) * a.B + L.cg * LC);
-#pragma unroll
-            for (int q = 0; q < LC / 4; ++q) {
-              const float4 x = __ldcg(ps_ + q);
-              tot[4 * q] += x.x; tot[4 * q + 1] += x.y; tot[4 * q + 2] += x.z; tot[4 * q + 3] += x.w;
-            }
-          }
-          reduce_groups<LC>(tot, L.CG);
-          if (L.lane == 0) a.cnt[row] = 0;
-          if (g == 0) {
-#pragma unroll
-            for (int h = 0; h < LC / 8; ++h) {
-              const V8 pv = Store<TP>::load(a.qprev, row, a.B, L.cg * (LC / 8) + h);
-#pragma unroll
-              for (int i = 0; i < 8; ++i) prev[8 * h + i] = pv.x[i];
-            }
-            const float4* yrow = reinterpret_cast<const float4*>(a.y + row * a.B + L.cg * LC);
-#pragma unroll
-            for (int i = 0; i < LC / 4; ++i) {
-              const float4 x = yrow[i];
-              yv[4 * i] = x.x; yv[4 * i + 1] = x.y; yv[4 * i + 2] = x.z; yv[4 * i + 3] = x.w;
-            }
-            update_seg<TO, LC>(L, row, (float)a.ldeg[row], tot, prev, yv, nrm);
-          }
-        }
+        if (old == np - 1) finish_long_row<TP, TO, LC>(L, row, slot0, np, nrm);
       }
     } else if (!CHUNK) {
-      if (ct < G + OP) {
-        if (g == 0) put_prev<TP, LC, C::PW>(prev, ct - G, src);
-      } else {
-        if (g == 0) put_f32<LC, C::PW>(yv, ct - G - OP, src);
-        if (ct == rpr - 1) {
-          reduce_groups<LC>(acc, L.CG);
-          if (g == 0) update_seg<TO, LC>(L, t.row0 + cs, (float)d, acc, prev, yv, nrm);
+      if (c_own == 0) {  // the row's sums, before its first own piece
+        reduce_groups<LC>(acc, L.CG);
+        Store<TG>::template finish<LC>(acc);
+      }
+      if (g == 0) own_round<TP, TO, LC, SB, OP, C::OY>(L, t.row0 + c_seq, (float)d, c_own, src, acc, nrm);
+      if (++c_own == OWN) {
 #pragma unroll
-          for (int i = 0; i < LC; ++i) acc[i] = 0.f;
-        }
+        for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+        c_own = 0;
+        ++c_seq;
+        c_left = G;
+        c_j = g;
       }
     }
-    if (++ct == rpr) {
-      ct = 0;
-      ++cs;
-    }
-    issue((rc + S - 1) & (S - 1));
+    c_off = (c_off + C::kStride) & C::kMask;
+    issue();
     bcommit();
   }
 }
@@ -610,12 +682,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   L.pol_stream = bpolicy_evict_first();
   L.ring = (uint32_t)__cvta_generic_to_shared(ring) + lane * C::SB;
   L.ring_p = ring + lane * C::SB;
-  L.qcur = static_cast<const unsigned char*>(a.qcur);
+  L.qseg = static_cast<const unsigned char*>(a.qcur) + (size_t)L.cg * C::SB;
+  L.pseg = static_cast<const unsigned char*>(a.qprev) + (size_t)L.cg * LC * C::sP;
+  L.yseg = reinterpret_cast<const unsigned char*>(a.y) + (size_t)L.cg * LC * 4;
   L.zero = static_cast<const unsigned char*>(a.zero) + L.cg * C::SB;
-  L.rowG = (size_t)a.B * C::sG;
+  L.rowG = (uint32_t)(a.B * C::sG);
   L.rowP = (size_t)a.B * C::sP;
-  L.segG = (size_t)L.cg * C::SB;
-  L.segP = (size_t)L.cg * LC * C::sP;
+  L.rowY = (size_t)a.B * 4;
   float nrm[LC];
 #pragma unroll
   for (int i = 0; i < LC; ++i) nrm[i] = 0.f;
@@ -685,28 +758,22 @@ __global__ void control_kernel(ColState* col, const ColParam* par, ColStat* stat
   st.k += 1;
 }
 
-// Zero the given columns of Q_a, Q_b (and the 16-bit pair) and y over all rows.
-template <typename T>
-__device__ __forceinline__ void zero_col(void* base, int64_t row, int B, int j) {
-  static_cast<T*>(base)[row * B + j] = T(0.0f);
-}
-
-__global__ void reset_columns_kernel(int64_t na, int B, const int* cols, int ncols, float* fa, float* fb, void* ha,
-                                     void* hb, int h_is_bf16, float* y) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < na; r += (int64_t)gridDim.x * blockDim.x) {
-    for (int t = 0; t < ncols; ++t) {
-      const int j = cols[t];
-      fa[r * B + j] = 0.f;
-      fb[r * B + j] = 0.f;
-      y[r * B + j] = 0.f;
+// Zero the given columns of Q_a, Q_b (and the 16-bit pair) and y over all
+// rows: a warp per row, its lanes over the listed columns (one row's writes
+// share its cache lines).
+__global__ void reset_columns_kernel(int64_t na, int B, const int* cols, int ncols, float* fa, float* fb,
+                                     uint16_t* ha, uint16_t* hb, float* y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
+    for (int t = lane; t < ncols; t += 32) {
+      const int64_t i = r * B + cols[t];
+      fa[i] = 0.f;
+      fb[i] = 0.f;
+      y[i] = 0.f;
       if (ha) {
-        if (h_is_bf16) {
-          zero_col<__nv_bfloat16>(ha, r, B, j);
-          zero_col<__nv_bfloat16>(hb, r, B, j);
-        } else {
-          zero_col<__half>(ha, r, B, j);
-          zero_col<__half>(hb, r, B, j);
-        }
+        ha[i] = 0;  // +0 in BF16 and FP16
+        hb[i] = 0;
       }
     }
   }
@@ -783,7 +850,9 @@ void launch_spmm_lc(const SpmmArgs& a, cudaStream_t st) {
   GP_LAUNCHED();
 }
 
-// 16-bit gathers: a lane owns 16 columns (32 bytes per round) when B >= 16.
+// With 16-bit gathers a lane owns 16 columns (32 bytes per round) when
+// B >= 16; FP32 gathers keep 8 columns per lane, so that a round stays 32
+// bytes and the ring holds 8 rounds.
 template <typename TG, typename TP, typename TO>
 void launch_spmm(const SpmmArgs& a, cudaStream_t st) {
   if constexpr (sizeof(TG) == 2) {
@@ -1004,9 +1073,20 @@ std::vector<int> ColumnEngine::admit(const std::vector<gp_request>& reqs, std::v
   }
   GP_CUDA_TRY(cudaStreamSynchronize(st_));  // host vectors above are pageable and local
   const int sms = device_sms();
-  reset_columns_kernel<<<sms * 4, 256, 0, st_>>>(g_.n_active, B_, d_cols, nc, f_[0], f_[1], h_[0], h_[1],
-                                                  storage_ == GP_BF16 ? 1 : 0, y_);
-  GP_LAUNCHED();
+  const size_t cells = (size_t)std::max<int64_t>(g_.n_active, 1) * B_;
+  if (nc == B_) {  // a whole new block: clear the buffers outright
+    GP_CUDA_TRY(cudaMemsetAsync(f_[0], 0, sizeof(float) * cells, st_));
+    GP_CUDA_TRY(cudaMemsetAsync(f_[1], 0, sizeof(float) * cells, st_));
+    GP_CUDA_TRY(cudaMemsetAsync(y_, 0, sizeof(float) * cells, st_));
+    if (h_[0]) {
+      GP_CUDA_TRY(cudaMemsetAsync(h_[0], 0, 2 * cells, st_));
+      GP_CUDA_TRY(cudaMemsetAsync(h_[1], 0, 2 * cells, st_));
+    }
+  } else {
+    reset_columns_kernel<<<sms * 8, 256, 0, st_>>>(g_.n_active, B_, d_cols, nc, f_[0], f_[1], (uint16_t*)h_[0],
+                                                    (uint16_t*)h_[1], y_);
+    GP_LAUNCHED();
+  }
   // Q_1 goes to the buffer the next pass gathers (pass_ & 1), Q_0 to the other.
   float* q1 = f_[pass_ & 1];
   float* q0 = f_[(pass_ + 1) & 1];
