@@ -93,25 +93,33 @@ __device__ __forceinline__ BTile decode_btile(int4 t) {
                (int)(m >> 17)};
 }
 
-// ---- cache policies and asynchronous copies
-__device__ __forceinline__ uint64_t bpolicy_evict_first() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t bpolicy_evict_last() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void bcp16(uint32_t dst, const void* src, uint64_t pol) {
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
-               : "memory");
-}
+// ---- asynchronous-copy groups
 __device__ __forceinline__ void bcommit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void bwait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// SB bytes from global to shared memory in 16-byte cp.async copies.
+template <int SB>
+__device__ __forceinline__ void cp_seg(uint32_t dst, const unsigned char* src) {
+  if constexpr (SB == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  } else if constexpr (SB == 32) {
+    asm volatile(
+        "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+        "cp.async.cg.shared.global [%0+16], [%1+16], 16;" ::"r"(dst),
+        "l"(src)
+        : "memory");
+  } else {
+    asm volatile(
+        "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
+        "cp.async.cg.shared.global [%0+16], [%1+16], 16;\n\t"
+        "cp.async.cg.shared.global [%0+32], [%1+32], 16;\n\t"
+        "cp.async.cg.shared.global [%0+48], [%1+48], 16;" ::"r"(dst),
+        "l"(src)
+        : "memory");
+  }
 }
 
 // ---- 8-column vectors of each storage type
@@ -142,10 +150,13 @@ struct Store<float> {
     const float4 a = __ldg(p), b = __ldg(p + 1);
     return V8{{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w}};
   }
-  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
-    float4* p = reinterpret_cast<float4*>(static_cast<float*>(base) + row * B + cg * 8);
+  __device__ static __forceinline__ void st8(unsigned char* at, const V8& v) {
+    float4* p = reinterpret_cast<float4*>(at);
     p[0] = make_float4(v.x[0], v.x[1], v.x[2], v.x[3]);
     p[1] = make_float4(v.x[4], v.x[5], v.x[6], v.x[7]);
+  }
+  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+    st8(reinterpret_cast<unsigned char*>(static_cast<float*>(base) + row * B + cg * 8), v);
   }
 };
 
@@ -178,14 +189,17 @@ struct Store<__nv_bfloat16> {
     decode(__ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * B + cg * 8)), v.x);
     return v;
   }
-  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+  __device__ static __forceinline__ void st8(unsigned char* at, const V8& v) {
     uint32_t u[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const __nv_bfloat162 h = __floats2bfloat162_rn(v.x[2 * i], v.x[2 * i + 1]);
       u[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(base) + row * B + cg * 8) = make_uint4(u[0], u[1], u[2], u[3]);
+    *reinterpret_cast<uint4*>(at) = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+    st8(reinterpret_cast<unsigned char*>(static_cast<__nv_bfloat16*>(base) + row * B + cg * 8), v);
   }
 };
 
@@ -223,14 +237,17 @@ struct Store<__half> {
     decode(__ldg(reinterpret_cast<const uint4*>(static_cast<const __half*>(base) + row * B + cg * 8)), v.x);
     return v;
   }
-  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+  __device__ static __forceinline__ void st8(unsigned char* at, const V8& v) {
     uint32_t u[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const __half2 h = __floats2half2_rn(v.x[2 * i] * kF16Scale, v.x[2 * i + 1] * kF16Scale);
       u[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    *reinterpret_cast<uint4*>(static_cast<__half*>(base) + row * B + cg * 8) = make_uint4(u[0], u[1], u[2], u[3]);
+    *reinterpret_cast<uint4*>(at) = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+  __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
+    st8(reinterpret_cast<unsigned char*>(static_cast<__half*>(base) + row * B + cg * 8), v);
   }
 };
 
@@ -279,33 +296,37 @@ struct Geo {
   static_assert(SB == 16 || SB == 32 || SB == 64, "a round moves 16, 32 or 64 bytes per lane");
 };
 
-// Per-lane constants of the pass.
+// Per-lane constants of the pass.  The loops read these register copies
+// rather than the kernel arguments: the memory clobbers of the cp.async
+// statements would force every argument read from memory to be repeated after
+// each copy.
 struct Lane {
-  const SpmmArgs* a;
-  const ColState* s_col;
+  const SpmmArgs* a;            // (chunk and finisher paths only)
+  const ColState* s_col;        // state of this lane's first column
   uint32_t ring;                // shared address of this lane's slot 0
   const unsigned char* ring_p;  // the same, generic
   const unsigned char* qseg;    // Q_k + this lane's segment offset
   const unsigned char* pseg;    // Q_{k-1} + this lane's segment offset
-  const unsigned char* yseg;    // y + this lane's segment offset
+  unsigned char* nseg;          // Q_{k+1} + this lane's segment offset
+  unsigned char* yseg;          // y + this lane's segment offset
   const unsigned char* zero;    // zero segment
-  uint32_t rowG;                // bytes of a Q_k row
-  size_t rowP, rowY;            // bytes of a Q_{k-1} row, of a y row
-  uint64_t pol_keep, pol_stream;
+  uint32_t rowG, rowP, rowN, rowY;  // row bytes of Q_k, Q_{k-1}, Q_{k+1}, y
+  int na;
   int cg, g, CG, EG, lane;
 };
 
 // Source of the gathered segment of neighbour v (rows beyond the active ones,
 // which only an unvalidated asymmetric CSR can list, read zeros).
 __device__ __forceinline__ const unsigned char* gather_src(const Lane& L, int v) {
-  return v < L.a->na ? L.qseg + (uint64_t)(uint32_t)v * L.rowG : L.zero;
+  return v < L.na ? L.qseg + (uint64_t)(uint32_t)v * L.rowG : L.zero;
 }
 
 // Source of piece o (SB bytes) of row u's own Q_{k-1} segment (o < OP) or y
 // segment.
 template <int SB, int OP>
 __device__ __forceinline__ const unsigned char* own_src(const Lane& L, int64_t u, int o) {
-  return o < OP ? L.pseg + (size_t)u * L.rowP + (size_t)o * SB : L.yseg + (size_t)u * L.rowY + (size_t)(o - OP) * SB;
+  return o < OP ? L.pseg + (uint64_t)(uint32_t)u * L.rowP + o * SB
+                : L.yseg + (uint64_t)(uint32_t)u * L.rowY + (o - OP) * SB;
 }
 
 // Add one gathered segment (LC values of TG) from a ring slot.
@@ -318,38 +339,14 @@ __device__ __forceinline__ void add_seg(const unsigned char* p, float acc[LC]) {
 // Copy a tile's col_idx entries [e0, e0 + len) into a warp's staging buffer
 // with 16-byte copies from the aligned-down start; entry e0 + i lands at
 // index (e0 & 3) + i.  (col_idx is padded so the last vector is in bounds.)
-__device__ __forceinline__ void stage_indices(int* buf, const int32_t* ci, int64_t e0, int len, int lane,
-                                              uint64_t pol) {
+__device__ __forceinline__ void stage_indices(int* buf, const int32_t* ci, int64_t e0, int len, int lane) {
   const int64_t a0 = e0 & ~(int64_t)3;
   const int nvec = (int)((e0 + len - a0 + 3) >> 2);
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
-  for (int v = lane; v < nvec; v += 32) bcp16(base + 16u * v, ci + a0 + 4 * v, pol);
+  for (int v = lane; v < nvec; v += 32) cp_seg<16>(base + 16u * v, reinterpret_cast<const unsigned char*>(ci + a0 + 4 * v));
 }
 
 __device__ __forceinline__ int tile_len(const BTile& t) { return t.kind == 2 ? t.b : t.a * t.b; }
-
-// SB bytes from global to shared memory in 16-byte cp.async copies.
-template <int SB>
-__device__ __forceinline__ void cp_seg(uint32_t dst, const unsigned char* src, uint64_t pol) {
-  if constexpr (SB == 16) {
-    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
-                 : "memory");
-  } else if constexpr (SB == 32) {
-    asm volatile(
-        "cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n\t"
-        "cp.async.cg.shared.global.L2::cache_hint [%0+16], [%1+16], 16, %2;" ::"r"(dst),
-        "l"(src), "l"(pol)
-        : "memory");
-  } else {
-    asm volatile(
-        "cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n\t"
-        "cp.async.cg.shared.global.L2::cache_hint [%0+16], [%1+16], 16, %2;\n\t"
-        "cp.async.cg.shared.global.L2::cache_hint [%0+32], [%1+32], 16, %2;\n\t"
-        "cp.async.cg.shared.global.L2::cache_hint [%0+48], [%1+48], 16, %2;" ::"r"(dst),
-        "l"(src), "l"(pol)
-        : "memory");
-  }
-}
 
 // The row update, applied as row u's own segments land (after its gathers,
 // so acc holds the final neighbour sums).  A Q_{k-1} piece (columns C0 ..
@@ -378,21 +375,21 @@ __device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, co
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int c = C0 + 8 * h + i;
-      const ColState cs = L.s_col[L.cg * LC + c];
+      const ColState cs = L.s_col[c];
       const float p = prev[8 * h + i];
       const float r = 2.0f * acc[c] - d * p;
       out.x[i] = cs.active ? r * inv : p;
       acc[c] = cs.active ? r : 0.f;
       nrm[c] += fabsf(acc[c]);
     }
-    Store<TO>::store(L.a->qnext, u, L.a->B, L.cg * (LC / 8) + C0 / 8 + h, out);
+    Store<TO>::st8(L.nseg + (uint64_t)(uint32_t)u * L.rowN + (C0 / 8 + h) * 8 * Store<TO>::bytes, out);
   }
 }
 
 template <int LC, int PW, int C0>
 __device__ __forceinline__ void y_piece(const Lane& L, int64_t u, const unsigned char* src, const float acc[LC]) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
-  float4* yrow = reinterpret_cast<float4*>(L.a->y + u * L.a->B + L.cg * LC + C0);
+  float4* yrow = reinterpret_cast<float4*>(L.yseg + (uint64_t)(uint32_t)u * L.rowY + C0 * 4);
 #pragma unroll
   for (int q = 0; q < PW / 4; ++q) {
     float4 x = s4[q];
@@ -400,7 +397,7 @@ __device__ __forceinline__ void y_piece(const Lane& L, int64_t u, const unsigned
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int c = C0 + 4 * q + k;
-      const ColState cs = L.s_col[L.cg * LC + c];
+      const ColState cs = L.s_col[c];
       xv[k] = fmaf(cs.active ? cs.coef : 0.f, acc[c], xv[k]);
     }
     yrow[q] = x;
@@ -452,11 +449,11 @@ __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& 
     if (p_seq < nseq) {
       const uint32_t dst = L.ring + p_off;
       if (p_left > 0) {
-        if (p_row < nrows) cp_seg<SB>(dst, gather_src(L, *p_ci), L.pol_keep);
+        if (p_row < nrows) cp_seg<SB>(dst, gather_src(L, *p_ci));
         ++p_ci;
         --p_left;
       } else {
-        if (p_row < nrows) cp_seg<SB>(dst, own_src<SB, OP>(L, t.row0 + p_row, p_own), L.pol_stream);
+        if (p_row < nrows) cp_seg<SB>(dst, own_src<SB, OP>(L, t.row0 + p_row, p_own));
         if (++p_own == OWN) {
           p_own = 0;
           ++p_seq;
@@ -532,7 +529,7 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int c = 8 * h + i;
-        const ColState cs = L.s_col[L.cg * LC + c];
+        const ColState cs = L.s_col[c];
         const float r = 2.0f * tot[c] - d * pv.x[i];
         out.x[i] = cs.active ? r * inv : pv.x[i];
         tot[c] = cs.active ? r : 0.f;
@@ -547,7 +544,7 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
       float* xv = reinterpret_cast<float*>(&x);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const ColState cs = L.s_col[L.cg * LC + 4 * q + k];
+        const ColState cs = L.s_col[4 * q + k];
         xv[k] = fmaf(cs.active ? cs.coef : 0.f, tot[4 * q + k], xv[k]);
       }
       yrow[q] = x;
@@ -576,12 +573,12 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
     if (p_seq < nseq) {
       const uint32_t dst = L.ring + p_off;
       if (p_left > 0) {
-        if (p_j < d) cp_seg<SB>(dst, gather_src(L, *p_ci), L.pol_keep);
+        if (p_j < d) cp_seg<SB>(dst, gather_src(L, *p_ci));
         p_ci += EG;
         p_j += EG;
         if (--p_left == 0 && CHUNK) ++p_seq;
       } else {
-        if (g == 0) cp_seg<SB>(dst, own_src<SB, OP>(L, t.row0 + p_seq, p_own), L.pol_stream);
+        if (g == 0) cp_seg<SB>(dst, own_src<SB, OP>(L, t.row0 + p_seq, p_own));
         if (++p_own == OWN) {
           p_own = 0;
           ++p_seq;
@@ -672,23 +669,24 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   __syncthreads();
   Lane L;
   L.a = &a;
-  L.s_col = s_col;
   L.CG = a.B / LC;
   L.EG = 32 / L.CG;
   L.cg = lane % L.CG;
   L.g = lane / L.CG;
   L.lane = lane;
-  L.pol_keep = bpolicy_evict_last();
-  L.pol_stream = bpolicy_evict_first();
+  L.s_col = s_col + L.cg * LC;
   L.ring = (uint32_t)__cvta_generic_to_shared(ring) + lane * C::SB;
   L.ring_p = ring + lane * C::SB;
   L.qseg = static_cast<const unsigned char*>(a.qcur) + (size_t)L.cg * C::SB;
   L.pseg = static_cast<const unsigned char*>(a.qprev) + (size_t)L.cg * LC * C::sP;
-  L.yseg = reinterpret_cast<const unsigned char*>(a.y) + (size_t)L.cg * LC * 4;
+  L.nseg = static_cast<unsigned char*>(a.qnext) + (size_t)L.cg * LC * Store<TO>::bytes;
+  L.yseg = reinterpret_cast<unsigned char*>(a.y) + (size_t)L.cg * LC * 4;
   L.zero = static_cast<const unsigned char*>(a.zero) + L.cg * C::SB;
   L.rowG = (uint32_t)(a.B * C::sG);
-  L.rowP = (size_t)a.B * C::sP;
-  L.rowY = (size_t)a.B * 4;
+  L.rowP = (uint32_t)(a.B * C::sP);
+  L.rowN = (uint32_t)(a.B * Store<TO>::bytes);
+  L.rowY = (uint32_t)(a.B * 4);
+  L.na = (int)a.na;
   float nrm[LC];
 #pragma unroll
   for (int i = 0; i < LC; ++i) nrm[i] = 0.f;
@@ -699,7 +697,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   if (w < a.ntiles) {
     cur = a.tiles[w];
     const BTile t0 = decode_btile(cur);
-    stage_indices(s_ci, a.ci, t0.e0, tile_len(t0), lane, L.pol_stream);
+    stage_indices(s_ci, a.ci, t0.e0, tile_len(t0), lane);
     bcommit();
     bwait<0>();
     if (w + nwarps < a.ntiles) nd = a.tiles[w + nwarps];
@@ -710,7 +708,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
     const int* ci_t = s_ci + buf * kBTileSpan + (int)(t.e0 & 3);
     if (w + nwarps < a.ntiles) {  // the next tile's indices join this tile's first copy group
       const BTile tn = decode_btile(nd);
-      stage_indices(s_ci + (buf ^ 1) * kBTileSpan, a.ci, tn.e0, tile_len(tn), lane, L.pol_stream);
+      stage_indices(s_ci + (buf ^ 1) * kBTileSpan, a.ci, tn.e0, tile_len(tn), lane);
     }
     int4 nd2 = make_int4(0, 0, 0, 0);
     if (w + 2 * nwarps < a.ntiles) nd2 = a.tiles[w + 2 * nwarps];
