@@ -60,6 +60,12 @@ def parse():
                    help="comma list of the forms to time (the single-source form is always run)")
     p.add_argument("--batch-storage", default="bf16,fp32", help="storages of the batched form")
     p.add_argument("--batch-reps", type=int, default=3)
+    p.add_argument("--workload", default="rmat22",
+                   choices=["rmat22", "rmat24_mixed", "chunglu24_serve", "rmat26_int64"],
+                   help="rmat22: the headline single-source workload; the others time the batched and "
+                        "served forms on the larger graphs")
+    p.add_argument("--requests", type=int, default=10000, help="chunglu24_serve: requests per load level")
+    p.add_argument("--loads", default="0.5,0.8,0.95", help="chunglu24_serve: offered load levels")
     return p.parse_args()
 
 
@@ -67,16 +73,31 @@ BATCH_FORMS = {"bf16": ("bf16_tol1e-4", "GP_BF16", 1e-4), "fp16": ("fp16_tol1e-4
                "fp32": ("fp32_tol1e-6", "GP_F32", 1e-6), "fp32_1e-4": ("fp32_tol1e-4", "GP_F32", 1e-4)}
 
 
-def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32"), reps=3):
-    """gp_batch over the step's queries as one block: BF16/FP16 storage (FP32
-    warm-up) at l1 <= 1e-4, FP32 storage at l1 <= 1e-6; queries/s over `reps` runs."""
+def time_single(gp, dg, queries, tol, dev):
+    """The single-source form (one query at a time) on the given queries."""
+    import torch
+    y = torch.empty(dg.n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for fn, s, p in queries:
+        (gp.gp_ppr if fn == 0 else gp.gp_hkpr)(dg, s, p, tol, y, info=False)
+    torch.cuda.synchronize()
+    return len(queries) / (time.perf_counter() - t0)
+
+
+def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32"), reps=3, width=128,
+                  single_value=None, single_tol=1e-6):
+    """gp_batch over the step's queries in blocks of `width` columns: BF16/FP16
+    storage (FP32 warm-up) at l1 <= 1e-4, FP32 storage at l1 <= 1e-6;
+    queries/s over `reps` runs, and the ratio to the single-source form at
+    the same tolerance on the same queries."""
     import torch
     res = {}
+    single = {single_tol: single_value} if single_value else {}
     for key in storages:
         name, storage_name, tol = BATCH_FORMS[key]
         storage = getattr(gp, storage_name)
-        dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=storage,
-                                block_width=min(256, len(queries)))
+        dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=storage, block_width=width)
         ys = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in queries]
         reqs = [gp.make_request(fn, s, p, tol, ys[i]) for i, (fn, s, p) in enumerate(queries)]
         infos = gp.gp_batch(dg, reqs)  # warm-up (allocates the blocks)
@@ -87,8 +108,12 @@ def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32
             infos = gp.gp_batch(dg, reqs)
         torch.cuda.synchronize()
         dt = dist_max(time.perf_counter() - t0, world, dev)
-        res[name] = {"value": len(queries) * reps * world / dt, "unit": UNIT, "block_width": len(queries),
-                     "mean_K": float(np.mean([i["K"] for i in infos]))}
+        value = len(queries) * reps * world / dt
+        if tol not in single:  # whole-job rate: every rank at the slowest rank's pace
+            single[tol] = world / dist_max(1.0 / time_single(gp, dg_single, queries, tol, dev), world, dev)
+        res[name] = {"value": value, "unit": UNIT, "block_width": width, "queries": len(queries),
+                     "mean_K": float(np.mean([i["K"] for i in infos])),
+                     "single_source_same_tol": single[tol], "vs_single_source_same_tol": value / single[tol]}
         dg.close()
         del ys
     return res
@@ -389,7 +414,8 @@ def run_ours(args, rank, world):
     batched = None
     if not args.no_batched and "batched" in forms:
         batched = bench_batched(gp, dg, g, queries, dev, world, storages=args.batch_storage.split(","),
-                                reps=args.batch_reps)
+                                reps=args.batch_reps, width=args.batch_width, single_value=value,
+                                single_tol=args.tol)
     serving = None if args.no_batched or "serving" not in forms else bench_serving(gp, g, queries, dev, world)
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -428,11 +454,153 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------- the larger workloads
+
+MIXED_FUNCTIONS = [(0, 0.1), (0, 0.2), (0, 0.5), (1, 3.0), (1, 5.0), (1, 10.0)]
+
+
+def mixed_queries(srcs, seed):
+    """Columns cycling through SSPPR alpha in {0.1, 0.2, 0.5} and HKPR t in {3, 5, 10}."""
+    return [(MIXED_FUNCTIONS[i % 6][0], int(s), MIXED_FUNCTIONS[i % 6][1]) for i, s in enumerate(srcs)]
+
+
+def batched_forms(gp, g, queries, forms, width, reps, dev):
+    """gp_batch over `queries` for each (name, storage, tol): queries/s, K range, footprint."""
+    import torch
+    out = {}
+    for name, storage, tol in forms:
+        dg = gp.gp_graph_create(g.n, g.row_ptr if g.nnz > 2**31 - 1 else g.row_ptr32(), g.col_idx, g.degree,
+                                storage=storage, block_width=width)
+        ys = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range(min(width, len(queries)))]
+        reqs = [gp.make_request(fn, s, p, tol, ys[i % len(ys)]) for i, (fn, s, p) in enumerate(queries)]
+        free0 = torch.cuda.mem_get_info()[0]
+        infos = gp.gp_batch(dg, reqs)
+        torch.cuda.synchronize()
+        used = free0 - torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            infos = gp.gp_batch(dg, reqs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ks = [i["K"] for i in infos]
+        out[name] = {"value": len(queries) * reps / dt, "unit": UNIT, "l1_tol": tol, "block_width": width,
+                     "K_min": min(ks), "K_max": max(ks), "mean_K": float(np.mean(ks)),
+                     "k16_from": int(min(i["k16_from"] for i in infos)),
+                     "block_bytes": int(used)}
+        dg.close()
+        del ys
+    return out
+
+
+def serve_poisson(gp, g, dev, args):
+    """gp_submit/gp_poll under Poisson arrivals: the saturated rate first (all
+    requests at once), then each offered load as a fraction of it; latency is
+    arrival to completion (the service's own clock), per request."""
+    import torch
+    rng = np.random.default_rng(5)
+    nreq = args.requests
+    srcs = gg_sources(g, nreq, 6)
+    fns = rng.integers(0, 2, nreq)
+    params = [(0.1, 0.2, 0.5)[k] if f == 0 else (3.0, 5.0, 10.0)[k] for f, k in zip(fns, rng.integers(0, 3, nreq))]
+    tols = rng.choice([1e-4, 1e-5, 1e-6], nreq)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=256)
+    pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range(512)]
+    free = list(range(len(pool)))
+
+    def run(arrivals):
+        """Submit request i at arrivals[i] (seconds from start); returns (wall, latencies)."""
+        pending = {}
+        lat = []
+        t0 = time.perf_counter()
+        i = 0
+        while i < nreq or pending:
+            now = time.perf_counter() - t0
+            while i < nreq and arrivals[i] <= now and free:
+                b = free.pop()
+                r = gp.make_request(int(fns[i]), int(srcs[i]), float(params[i]), float(tols[i]), pool[b])
+                pending[gp.gp_submit(dg, r)] = b
+                i += 1
+            for tk in list(pending):
+                inf = gp.gp_poll(dg, tk)
+                if inf is not None:
+                    lat.append(inf["ms"])
+                    free.append(pending.pop(tk))
+            time.sleep(0.0002)
+        return time.perf_counter() - t0, lat
+
+    wall, lat = run(np.zeros(nreq))
+    sat = nreq / wall
+    res = {"saturated": {"value": sat, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99))}}
+    for load in [float(x) for x in args.loads.split(",")]:
+        gaps = rng.exponential(1.0 / (load * sat), nreq)
+        wall, lat = run(np.cumsum(gaps))
+        res[f"load_{load:g}"] = {"offered": load * sat, "value": nreq / wall, "unit": UNIT,
+                                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    stats = gp.gp_serve_stats(dg)
+    res["mean_active_columns"] = stats["mean_active"]
+    dg.close()
+    return res
+
+
+def gg_sources(g, k, seed):
+    import graphgen as gg
+    return gg.sources(g, k, seed)
+
+
+def run_workload(args, rank, world):
+    """The batched and served forms on the larger graphs (one GPU each; more
+    GPUs would run independent replicas)."""
+    import torch
+    import graphgen as gg
+    from paper_2412_10789_gb300 import build, gp
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    sampler = ClockSampler(local)
+    t_gen = time.perf_counter()
+    if args.workload == "rmat24_mixed":
+        g = gg.rmat(24, 16, 0.57, 0.19, 0.19, seed=3)
+        queries = mixed_queries(gg.sources(g, 256, 3), 3)
+        forms = [("bf16_tol1e-4", gp.GP_BF16, 1e-4), ("fp16_tol1e-4", gp.GP_F16, 1e-4),
+                 ("fp32_tol1e-4", gp.GP_F32, 1e-4), ("fp32_tol1e-6", gp.GP_F32, 1e-6)]
+        width, headline = 256, "bf16_tol1e-4"
+    elif args.workload == "rmat26_int64":
+        g = gg.rmat(26, 16, 0.57, 0.19, 0.19, seed=5)
+        queries = [(0, int(s), 0.2) for s in gg.sources(g, 64, 5)]
+        forms = [("bf16_tol1e-4", gp.GP_BF16, 1e-4), ("fp32_tol1e-4", gp.GP_F32, 1e-4)]
+        width, headline = 64, "bf16_tol1e-4"
+    else:
+        g = gg.chung_lu(1 << 24, 30.0, 2.1, seed=4)
+        queries, forms, width, headline = None, None, 256, None
+    t_gen = time.perf_counter() - t_gen
+    sampler.start()
+    if queries is not None:
+        res = batched_forms(gp, g, queries, forms, width, args.batch_reps, dev)
+        value, metric = res[headline]["value"], f"batched queries/s at l1<={forms[0][2]:g} ({args.workload})"
+    else:
+        res = serve_poisson(gp, g, dev, args)
+        value, metric = res["saturated"]["value"], "served queries/s, p50/p99 latency (chunglu24_serve)"
+    clocks = sampler.stop()
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/bf16/f16 storage, f32 accumulate",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "graph": g.name, "n": g.n, "nnz": g.nnz,
+                       "queries": len(queries) if queries else args.requests, "block_width": width,
+                       "generate_s": round(t_gen, 1), "parallelism": "replicas"},
+            "forms": res, "clocks": clocks}), flush=True)
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload != "rmat22":
+        run_workload(args, rank, world)
     else:
         run_ours(args, rank, world)
 

@@ -155,6 +155,9 @@ struct Store<float> {
     p[0] = make_float4(v.x[0], v.x[1], v.x[2], v.x[3]);
     p[1] = make_float4(v.x[4], v.x[5], v.x[6], v.x[7]);
   }
+  __device__ static __forceinline__ void st4(unsigned char* at, const float* v) {
+    *reinterpret_cast<float4*>(at) = make_float4(v[0], v[1], v[2], v[3]);
+  }
   __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
     st8(reinterpret_cast<unsigned char*>(static_cast<float*>(base) + row * B + cg * 8), v);
   }
@@ -197,6 +200,10 @@ struct Store<__nv_bfloat16> {
       u[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
     *reinterpret_cast<uint4*>(at) = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+  __device__ static __forceinline__ void st4(unsigned char* at, const float* v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2*>(at) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
   }
   __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
     st8(reinterpret_cast<unsigned char*>(static_cast<__nv_bfloat16*>(base) + row * B + cg * 8), v);
@@ -246,6 +253,11 @@ struct Store<__half> {
     }
     *reinterpret_cast<uint4*>(at) = make_uint4(u[0], u[1], u[2], u[3]);
   }
+  __device__ static __forceinline__ void st4(unsigned char* at, const float* v) {
+    const __half2 a = __floats2half2_rn(v[0] * kF16Scale, v[1] * kF16Scale);
+    const __half2 b = __floats2half2_rn(v[2] * kF16Scale, v[3] * kF16Scale);
+    *reinterpret_cast<uint2*>(at) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+  }
   __device__ static __forceinline__ void store(void* base, int64_t row, int B, int cg, const V8& v) {
     st8(reinterpret_cast<unsigned char*>(static_cast<__half*>(base) + row * B + cg * 8), v);
   }
@@ -267,7 +279,8 @@ struct SpmmArgs {
   int* cnt;             // long rows: chunks finished
   const void* zero;     // B zero values: the gather source of a neighbour beyond the active rows
   int64_t na;           // rows of the blocks (nodes with degree >= 1)
-  int B;
+  int B;                // columns of this pass (a prefix of each row)
+  int ldb;              // row stride of the blocks, in elements
 };
 
 // Combine the entry groups' partial sums (lanes cg, cg + CG, cg + 2 CG, ...).
@@ -365,24 +378,33 @@ __device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, co
       prev[4 * q] = x.x; prev[4 * q + 1] = x.y; prev[4 * q + 2] = x.z; prev[4 * q + 3] = x.w;
     }
   } else {
+    static_assert(PC % 8 == 0, "a 16-bit Q_{k-1} segment is one round of whole 8-column groups");
 #pragma unroll
     for (int h = 0; h < PC / 8; ++h) Store<TP>::decode(Store<TP>::lds(src + 16 * h), prev + 8 * h);
   }
   const float inv = 1.0f / d;
+  float out[PC];
 #pragma unroll
-  for (int h = 0; h < PC / 8; ++h) {
-    V8 out;
+  for (int i = 0; i < PC; ++i) {
+    const int c = C0 + i;
+    const ColState cs = L.s_col[c];
+    const float r = 2.0f * acc[c] - d * prev[i];
+    out[i] = cs.active ? r * inv : prev[i];
+    acc[c] = cs.active ? r : 0.f;
+    nrm[c] += fabsf(acc[c]);
+  }
+  unsigned char* dst = L.nseg + (uint64_t)(uint32_t)u * L.rowN + C0 * Store<TO>::bytes;
+  if constexpr (PC % 8 == 0) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int c = C0 + 8 * h + i;
-      const ColState cs = L.s_col[c];
-      const float p = prev[8 * h + i];
-      const float r = 2.0f * acc[c] - d * p;
-      out.x[i] = cs.active ? r * inv : p;
-      acc[c] = cs.active ? r : 0.f;
-      nrm[c] += fabsf(acc[c]);
+    for (int h = 0; h < PC / 8; ++h) {
+      V8 o8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) o8.x[i] = out[8 * h + i];
+      Store<TO>::st8(dst + h * 8 * Store<TO>::bytes, o8);
     }
-    Store<TO>::st8(L.nseg + (uint64_t)(uint32_t)u * L.rowN + (C0 / 8 + h) * 8 * Store<TO>::bytes, out);
+  } else {
+    static_assert(PC == 4, "a Q_{k-1} piece holds 4, 8 or 16 columns");
+    Store<TO>::st4(dst, out);
   }
 }
 
@@ -524,7 +546,7 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
     const float inv = 1.0f / d;
 #pragma unroll
     for (int h = 0; h < LC / 8; ++h) {
-      const V8 pv = Store<TP>::load(a.qprev, row, a.B, L.cg * (LC / 8) + h);
+      const V8 pv = Store<TP>::load(a.qprev, row, a.ldb, L.cg * (LC / 8) + h);
       V8 out;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -535,9 +557,9 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
         tot[c] = cs.active ? r : 0.f;
         nrm[c] += fabsf(tot[c]);
       }
-      Store<TO>::store(a.qnext, row, a.B, L.cg * (LC / 8) + h, out);
+      Store<TO>::store(a.qnext, row, a.ldb, L.cg * (LC / 8) + h, out);
     }
-    float4* yrow = reinterpret_cast<float4*>(a.y + row * a.B + L.cg * LC);
+    float4* yrow = reinterpret_cast<float4*>(a.y + row * a.ldb + L.cg * LC);
 #pragma unroll
     for (int q = 0; q < LC / 4; ++q) {
       float4 x = yrow[q];
@@ -682,10 +704,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   L.nseg = static_cast<unsigned char*>(a.qnext) + (size_t)L.cg * LC * Store<TO>::bytes;
   L.yseg = reinterpret_cast<unsigned char*>(a.y) + (size_t)L.cg * LC * 4;
   L.zero = static_cast<const unsigned char*>(a.zero) + L.cg * C::SB;
-  L.rowG = (uint32_t)(a.B * C::sG);
-  L.rowP = (uint32_t)(a.B * C::sP);
-  L.rowN = (uint32_t)(a.B * Store<TO>::bytes);
-  L.rowY = (uint32_t)(a.B * 4);
+  L.rowG = (uint32_t)(a.ldb * C::sG);
+  L.rowP = (uint32_t)(a.ldb * C::sP);
+  L.rowN = (uint32_t)(a.ldb * Store<TO>::bytes);
+  L.rowY = (uint32_t)(a.ldb * 4);
   L.na = (int)a.na;
   float nrm[LC];
 #pragma unroll
@@ -773,6 +795,40 @@ __global__ void reset_columns_kernel(int64_t na, int B, const int* cols, int nco
         ha[i] = 0;  // +0 in BF16 and FP16
         hb[i] = 0;
       }
+    }
+  }
+}
+
+// Move columns perm[0 .. nb) of every row to columns 0 .. nb) in place: a
+// warp per row reads all the values it moves before it writes any.
+template <typename T>
+__device__ __forceinline__ void permute_row(T* base, int64_t r, int ldb, const int* perm, int nb, int lane) {
+  T v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int j = lane + 32 * i;
+    if (j < nb) v[i] = base[r * ldb + perm[j]];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int j = lane + 32 * i;
+    if (j < nb) base[r * ldb + j] = v[i];
+  }
+  __syncwarp();
+}
+
+__global__ void permute_columns_kernel(int64_t na, int ldb, const int* perm, int nb, float* fa, float* fb,
+                                       uint16_t* ha, uint16_t* hb, float* y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
+    permute_row(fa, r, ldb, perm, nb, lane);
+    permute_row(fb, r, ldb, perm, nb, lane);
+    permute_row(y, r, ldb, perm, nb, lane);
+    if (ha) {
+      permute_row(ha, r, ldb, perm, nb, lane);
+      permute_row(hb, r, ldb, perm, nb, lane);
     }
   }
 }
@@ -877,7 +933,7 @@ void launch_stage(const SpmmArgs& a, int stage, cudaStream_t st) {
 // ------------------------------------------------------------------ engine
 
 ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st)
-    : g_(g), B_(B), storage_(storage), st_(st) {
+    : g_(g), B_(B), bw_(B), storage_(storage), st_(st) {
   if (B < 8 || B > 256 || (B & (B - 1)))
     throw Error{GP_EINVAL, "block width must be a power of two in [8, 256]"};
   if (storage != GP_F32 && storage != GP_BF16 && storage != GP_F16)
@@ -1125,7 +1181,8 @@ void ColumnEngine::pass() {
   a.cnt = cnt_;
   a.zero = zero_;
   a.na = g_.n_active;
-  a.B = B_;
+  a.B = bw_;
+  a.ldb = B_;
   if (storage_ == GP_F16) launch_stage<__half>(a, stage, st_);
   else launch_stage<__nv_bfloat16>(a, stage, st_);
   ++pass_;
@@ -1299,6 +1356,8 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
             in.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
           }
         }
+        while (eng.active() > 0 && eng.compact()) {
+        }
       }
     }
   }
@@ -1310,8 +1369,62 @@ void free_batch_work(Graph& g) {
   g.batch = nullptr;
 }
 
+// Halve the pass width once at most half of it is busy: the busy columns move
+// to the front of every row (with their state), so later passes gather and
+// update only that prefix.  Only between passes, and only while no new columns
+// are admitted (gp_batch).
+bool ColumnEngine::compact() {
+  const int nb = bw_ / 2;
+  if (nb < 8) return false;
+  std::vector<int> perm;
+  for (int j = 0; j < bw_; ++j)
+    if (slots_[j].busy) perm.push_back(j);
+  if ((int)perm.size() > nb) return false;
+  for (int j = 0; j < bw_ && (int)perm.size() < nb; ++j)
+    if (!slots_[j].busy) perm.push_back(j);
+  int* d_perm = scratch_ + 2 * B_;
+  GP_CUDA_TRY(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st_));
+  permute_columns_kernel<<<device_sms() * 8, 256, 0, st_>>>(g_.n_active, B_, d_perm, nb, f_[0], f_[1],
+                                                            (uint16_t*)h_[0], (uint16_t*)h_[1], y_);
+  GP_LAUNCHED();
+  // per-column state: through the host (a few hundred KB)
+  std::vector<ColState> cs(B_), cs2(B_);
+  std::vector<ColParam> cp(B_), cp2(B_);
+  std::vector<ColStat> st(B_), st2(B_);
+  std::vector<float> nm(B_), nm2(B_);
+  GP_CUDA_TRY(cudaMemcpyAsync(cs.data(), col_, sizeof(ColState) * B_, cudaMemcpyDeviceToHost, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(cp.data(), par_, sizeof(ColParam) * B_, cudaMemcpyDeviceToHost, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(st.data(), stat_, sizeof(ColStat) * B_, cudaMemcpyDeviceToHost, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(nm.data(), norm_, sizeof(float) * B_, cudaMemcpyDeviceToHost, st_));
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  std::vector<Slot> sl(B_);
+  for (int j = 0; j < B_; ++j) {
+    cs2[j] = ColState{0, 0.f};
+    std::memset(&cp2[j], 0, sizeof(ColParam));
+    st2[j] = ColStat{0, 0, 0, 0.f};
+    nm2[j] = 0.f;
+  }
+  for (int j = 0; j < nb; ++j) {
+    const int o = perm[j];
+    cs2[j] = cs[o];
+    cp2[j] = cp[o];
+    st2[j] = st[o];
+    nm2[j] = nm[o];
+    sl[j] = slots_[o];
+  }
+  GP_CUDA_TRY(cudaMemcpyAsync(col_, cs2.data(), sizeof(ColState) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(par_, cp2.data(), sizeof(ColParam) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(stat_, st2.data(), sizeof(ColStat) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(norm_, nm2.data(), sizeof(float) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));  // the host vectors are local
+  slots_.swap(sl);
+  bw_ = nb;
+  return true;
+}
+
 void ColumnEngine::restart() {
   GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  bw_ = B_;
   pass_ = 0;
   h_pass_ = -1;
   warm_ = 0;

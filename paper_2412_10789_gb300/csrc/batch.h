@@ -72,6 +72,10 @@ class ColumnEngine {
   std::vector<Finished> collect(bool force_all);
   // Forget the pass count and the 16-bit schedule (no column may be busy).
   void restart();
+  // Move the busy columns into the first half of the pass width once at most
+  // half of it is busy (no admissions may follow until restart()).  Returns
+  // whether the width was halved.
+  bool compact();
 
  private:
   void release();
@@ -89,6 +93,7 @@ class ColumnEngine {
 
   Graph& g_;
   int B_;
+  int bw_ = 0;  // columns of each pass (a prefix of B_)
   gp_dtype storage_;
   cudaStream_t st_;
   int kcap_ = 0;

@@ -151,7 +151,7 @@ Serve* get_serve(Graph& g) {
   GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = g.cfg.mem_budget ? g.cfg.mem_budget : (size_t)(0.8 * (double)free_b);
   const size_t per_col = ColumnEngine::bytes_per_column(g, GP_F32);
-  int cap = g.cfg.block_width > 0 ? g.cfg.block_width : 256;
+  int cap = std::min(g.cfg.block_width > 0 ? g.cfg.block_width : 256, 256);  // the engine's widest block
   int width = 8;
   while (width * 2 <= cap && (size_t)(width * 2) * per_col <= budget) width *= 2;
   if ((size_t)width * per_col > budget) throw Error{GP_ENOMEM, "memory budget is below eight query columns"};

@@ -94,6 +94,25 @@ def test_batch_stop_rule_accuracy(gp, gname, storage, tol):
         dg.close()
 
 
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_batch_narrow_16bit_block(gp, storage):
+    """Eight columns per block: lanes own 8 columns and the FP32 -> 16-bit
+    transition passes split a lane's Q_{k-1} segment into 4-column pieces."""
+    g = graph("rmat14")
+    st = {"bf16": gp.GP_BF16, "f16": gp.GP_F16}[storage]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=8, storage=st)
+    try:
+        srcs = gg.sources(g, 12, 23)  # a block of 8, then a block of 4 (compacted to 8 columns)
+        ys = _outputs(g, len(srcs))
+        infos = gp.gp_batch(dg, _requests(gp, g, srcs, 1e-4, ys))
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            l1 = O.errors(g, O.chebypower(g, int(s), KINDS[fn], p, 150), ys[i].cpu().numpy())["l1"]
+            assert l1 <= 1e-4, (i, storage, l1, infos[i])
+    finally:
+        dg.close()
+
+
 def test_batch_host_outputs_and_isolated_source(gp):
     g = gg.from_edges(40, [(i, i + 1) for i in range(30)] + [(35, 36)], "path_with_isolated")
     dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=8)
