@@ -1154,8 +1154,16 @@ std::vector<int> ColumnEngine::admit(const std::vector<gp_request>& reqs, std::v
   return slots;
 }
 
-// One fused pass over all active columns (control kernel + SpMM step).
+// One fused pass over all active columns (control kernel + SpMM step).  The
+// pass covers the smallest power-of-two prefix of the columns (at least 8)
+// that holds every busy column, so a lightly loaded engine runs narrow passes.
 void ColumnEngine::pass() {
+  int last = -1;
+  for (int j = 0; j < B_; ++j)
+    if (slots_[j].busy) last = j;
+  int w = 8;
+  while (w < last + 1) w <<= 1;
+  bw_ = std::min(w, B_);
   control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_);
   GP_LAUNCHED();
   // storage stage of this pass: FP32 until every column's warm-up has passed
@@ -1371,8 +1379,8 @@ void free_batch_work(Graph& g) {
 
 // Halve the pass width once at most half of it is busy: the busy columns move
 // to the front of every row (with their state), so later passes gather and
-// update only that prefix.  Only between passes, and only while no new columns
-// are admitted (gp_batch).
+// update only that prefix.  Only between passes; columns admitted later take
+// the lowest free slots.
 bool ColumnEngine::compact() {
   const int nb = bw_ / 2;
   if (nb < 8) return false;

@@ -73,8 +73,7 @@ class ColumnEngine {
   // Forget the pass count and the 16-bit schedule (no column may be busy).
   void restart();
   // Move the busy columns into the first half of the pass width once at most
-  // half of it is busy (no admissions may follow until restart()).  Returns
-  // whether the width was halved.
+  // half of it is busy.  Returns whether the width was halved.
   bool compact();
 
  private:

@@ -9,7 +9,9 @@
 // columns (the per-column stop rule runs on the device in the pass's control
 // kernel), and every few passes collects the retired columns: their y is
 // written to the request's y_out, the ticket completes, and the column is free
-// for the next request.  Requests therefore join and leave the running block
+// for the next request.  Passes cover only the prefix of columns that holds
+// the busy ones, and the busy columns are moved to the front when at most
+// half of that prefix is busy, so a lightly loaded service runs narrow passes.  Requests therefore join and leave the running block
 // while the others keep going; their work shares every pass.
 #include <algorithm>
 #include <condition_variable>
@@ -113,6 +115,8 @@ struct Serve {
         if (++since_collect >= kCollectEvery) {
           since_collect = 0;
           auto fin = eng->collect(false);
+          while (eng->active() > 0 && eng->compact()) {
+          }
           std::lock_guard<std::mutex> lk(mu);
           for (const auto& f : fin) finish(f.tag, f.K, f.C, f.tail_bound);
         }
