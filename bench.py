@@ -103,17 +103,28 @@ def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32
         infos = gp.gp_batch(dg, reqs)  # warm-up (allocates the blocks)
         torch.cuda.synchronize()
         dist_barrier(world)
+        gp.gp_profile_enable(dg, True)
+        gp.gp_profile_read(dg)
         t0 = time.perf_counter()
         for _ in range(reps):
             infos = gp.gp_batch(dg, reqs)
         torch.cuda.synchronize()
         dt = dist_max(time.perf_counter() - t0, world, dev)
+        prof = gp.gp_profile_read(dg)
+        gp.gp_profile_enable(dg, False)
         value = len(queries) * reps * world / dt
         if tol not in single:  # whole-job rate: every rank at the slowest rank's pace
             single[tol] = world / dist_max(1.0 / time_single(gp, dg_single, queries, tol, dev), world, dev)
+        peak, peak_kind = measured_peaks()
+        ms = prof["step_ms"] / max(prof["step_launches"], 1)
+        achieved = prof["step_bytes"] / max(prof["step_launches"], 1) / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
         res[name] = {"value": value, "unit": UNIT, "block_width": width, "queries": len(queries),
                      "mean_K": float(np.mean([i["K"] for i in infos])),
-                     "single_source_same_tol": single[tol], "vs_single_source_same_tol": value / single[tol]}
+                     "single_source_same_tol": single[tol], "vs_single_source_same_tol": value / single[tol],
+                     "roofline": {"bound": "hbm", "kernel": "spmm_step_kernel", "achieved": achieved, "peak": peak,
+                                  "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                                  "mean_launch_ms": ms, "launches": prof["step_launches"],
+                                  "spmm_share_of_wall": prof["step_ms"] / 1000.0 / dt}}
         dg.close()
         del ys
     return res

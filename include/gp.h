@@ -224,8 +224,10 @@ uint64_t gp_launch_count(void);
 
 /* Kernel timing: while enabled, the fused Chebyshev step kernels of
  * gp_ppr / gp_hkpr / gp_query / gp_batch are bracketed by CUDA events on their
- * stream; gp_profile_read returns the summed device time (ms) and launch count
- * of the launches that did work since the last read, and resets them. */
+ * stream; gp_profile_read returns the summed device time (ms), the launch count
+ * and the algorithmic bytes (col_idx once, Q_k gathered once, Q_{k-1} read,
+ * Q_{k+1} written, y read and written) of the launches that did work since the
+ * last read, and resets them. */
 gp_status gp_profile_enable(gp_graph* g, int on);
 gp_status gp_profile_read(gp_graph* g, double* step_ms, int64_t* step_launches,
                           double* step_bytes);

@@ -1016,6 +1016,8 @@ ColumnEngine::~ColumnEngine() { release(); }
 
 void ColumnEngine::release() {
   if (st_) cudaStreamSynchronize(st_);
+  for (cudaEvent_t e : events_) cudaEventDestroy(e);
+  events_.clear();
   Allocator& A = g_.alloc;
   for (void* p : {(void*)f_[0], (void*)f_[1], h_[0], h_[1], (void*)y_, (void*)col_, (void*)par_, (void*)stat_,
                   (void*)norm_, (void*)scratch_, outs_, stage_, (void*)tiles_, (void*)poff_, (void*)ldeg_,
@@ -1191,8 +1193,24 @@ void ColumnEngine::pass() {
   a.na = g_.n_active;
   a.B = bw_;
   a.ldb = B_;
+  const bool prof = profile_;
+  if (prof) {
+    while (events_.size() < prof_marks_.size() * 2 + 2) {
+      cudaEvent_t e;
+      GP_CUDA_TRY(cudaEventCreate(&e));
+      events_.push_back(e);
+    }
+    GP_CUDA_TRY(cudaEventRecord(events_[prof_marks_.size() * 2], st_));
+  }
   if (storage_ == GP_F16) launch_stage<__half>(a, stage, st_);
   else launch_stage<__nv_bfloat16>(a, stage, st_);
+  if (prof) {
+    GP_CUDA_TRY(cudaEventRecord(events_[prof_marks_.size() * 2 + 1], st_));
+    // algorithmic bytes: col_idx once, Q_k gathered once, Q_{k-1} read,
+    // Q_{k+1} written, y read and written, over the pass's columns
+    const int sg = stage >= 2 ? 2 : 4, sp = stage >= 3 ? 2 : 4, so = stage >= 1 ? 2 : 4;
+    prof_marks_.push_back(4.0 * (double)g_.nnz + (double)g_.n_active * bw_ * (sg + sp + so + 8));
+  }
   ++pass_;
   ++passes_total_;
 }
@@ -1332,6 +1350,7 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
   }
   ColumnEngine& eng = *bc->eng;
   eng.restart();
+  eng.set_profile(g.profiling);
   auto t0 = std::chrono::steady_clock::now();
   for (int base = 0; base < count; base += B) {
     const int nb = std::min(B, count - base);
@@ -1368,6 +1387,7 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
         }
       }
     }
+    eng.flush_profile();
   }
 }
 
@@ -1428,6 +1448,20 @@ bool ColumnEngine::compact() {
   slots_.swap(sl);
   bw_ = nb;
   return true;
+}
+
+// Add the timed passes to the graph's profile counters (gp_profile_read).
+void ColumnEngine::flush_profile() {
+  if (prof_marks_.empty()) return;
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  for (size_t i = 0; i < prof_marks_.size(); ++i) {
+    float ms = 0.f;
+    GP_CUDA_TRY(cudaEventElapsedTime(&ms, events_[2 * i], events_[2 * i + 1]));
+    g_.prof_ms += ms;
+    g_.prof_launches += 1;
+    g_.prof_bytes += prof_marks_[i];
+  }
+  prof_marks_.clear();
 }
 
 void ColumnEngine::restart() {

@@ -75,6 +75,10 @@ class ColumnEngine {
   // Move the busy columns into the first half of the pass width once at most
   // half of it is busy.  Returns whether the width was halved.
   bool compact();
+  // Time each SpMM pass with CUDA events (gp_batch under gp_profile_enable);
+  // flush_profile() adds them to the graph's profile counters.
+  void set_profile(bool on) { profile_ = on; }
+  void flush_profile();
 
  private:
   void release();
@@ -120,6 +124,9 @@ class ColumnEngine {
   int h_pass_ = -1;
   int warm_ = 0;
   uint64_t passes_total_ = 0;
+  bool profile_ = false;
+  std::vector<cudaEvent_t> events_;
+  std::vector<double> prof_marks_;  // algorithmic bytes of each timed pass
 };
 
 struct BatchCache {

@@ -209,3 +209,29 @@ def test_destroy_with_pending_tickets(gp):
     for i, s in enumerate(gg.sources(g, 30, 3)):
         gp.gp_submit(dg, gp.make_request(0, int(s), 0.1, 1e-6, ys[i]))
     dg.close()  # must not hang or fault with work queued and in flight
+
+
+def test_batch_profile_counts_passes(gp):
+    """gp_profile_* time every SpMM pass of gp_batch and count its algorithmic bytes."""
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16)
+    try:
+        srcs = gg.sources(g, 6, 31)
+        ys = _outputs(g, len(srcs))
+        K = 9
+        reqs = [gp.make_request(0, int(s), 0.2, 1e-6, ys[i], k_rule=gp.GP_K_FIXED, k_fixed=K)
+                for i, s in enumerate(srcs)]
+        gp.gp_profile_enable(dg, True)
+        gp.gp_profile_read(dg)
+        gp.gp_batch(dg, reqs)
+        prof = gp.gp_profile_read(dg)
+        gp.gp_profile_enable(dg, False)
+        # passes k = 1 .. K-1 compute r_2 .. r_K; the control kernel retires the
+        # columns before the pass after the last, which still runs (empty)
+        assert K - 1 <= prof["step_launches"] <= K + 4
+        assert prof["step_ms"] > 0.0
+        na = int((g.degree > 0).sum())
+        per_pass_min = 4.0 * g.nnz + na * 8 * (4 + 4 + 4 + 8)  # the narrowest pass: 8 FP32 columns
+        assert prof["step_bytes"] >= prof["step_launches"] * per_pass_min
+    finally:
+        dg.close()
