@@ -71,7 +71,7 @@ typedef struct {
                               GP_F32, GP_BF16 or GP_F16 (16-bit ones with the FP32
                               warm-up schedule); single queries always use GP_F32 */
   int32_t block_width;     /* B, columns per batched SpMM pass; 0 = autotune */
-  int32_t autotune;        /* 1: time bucket thresholds / B on this graph at create */
+  int32_t autotune;        /* 1: gp_batch with block_width 0 uses the width gp_autotune picks */
   int32_t k_max;           /* hard cap on K (default 96) */
   int32_t validate_symmetry; /* 1 (default): check that every (u,v) has (v,u) */
   int32_t t_heavy;         /* rows with degree >= t_heavy are summed in pieces by several warps
@@ -180,6 +180,23 @@ gp_status gp_power(gp_graph* g, int32_t function, int32_t source, double param, 
  * receives `count` reports.
  */
 gp_status gp_batch(gp_graph* g, int32_t count, const gp_request* reqs, gp_query_info* infos);
+
+/*
+ * Autotuner for the batched form (the block width B; the paper has no
+ * counterpart).  Times fused SpMM passes of the column engine on this graph at
+ * each candidate width (powers of two in [8, 256]; widths == NULL means 32,
+ * 64, 128, 256) with CUDA events on the graph's stream, for `storage` (16-bit
+ * storage: 0.45 of an FP32 warm-up pass plus 0.55 of a 16-bit pass), and
+ * returns the width with the least device time per column and pass in
+ * *best_width, and that time in microseconds in *us_per_column_pass
+ * (nullable).  The default-candidate result is cached per graph structure (n,
+ * nnz and degree sequence), storage and device; gp_batch uses it when
+ * cfg.block_width is 0 and cfg.autotune is 1.  Allocates and frees one column
+ * block per candidate; candidates that need more than half of the free device
+ * memory are skipped (GP_EINVAL if none fits).
+ */
+gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int32_t nwidths, int32_t* best_width,
+                      double* us_per_column_pass);
 
 /*
  * Continuous-batching service.  gp_submit queues a request and returns a

@@ -39,6 +39,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "batch.h"
@@ -1159,7 +1162,7 @@ std::vector<int> ColumnEngine::admit(const std::vector<gp_request>& reqs, std::v
 // One fused pass over all active columns (control kernel + SpMM step).  The
 // pass covers the smallest power-of-two prefix of the columns (at least 8)
 // that holds every busy column, so a lightly loaded engine runs narrow passes.
-void ColumnEngine::pass() {
+void ColumnEngine::pass(int force_stage) {
   int last = -1;
   for (int j = 0; j < B_; ++j)
     if (slots_[j].busy) last = j;
@@ -1174,6 +1177,7 @@ void ColumnEngine::pass() {
     if (h_pass_ < 0 && pass_16_ok()) h_pass_ = pass_;
     if (h_pass_ >= 0) stage = std::min(3, pass_ - h_pass_ + 1);
   }
+  if (force_stage >= 0) stage = storage_ == GP_F32 ? 0 : force_stage;  // timing only (autotune)
   SpmmArgs a;
   a.tiles = tiles_;
   a.ntiles = ntiles_;
@@ -1336,7 +1340,13 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
       GP_REQUIRE(r.k_fixed >= 1 && r.k_fixed < g.cfg.k_max, "k_fixed must be in [1, k_max)");
   }
   if (count == 0) return;
-  const int B = g.cfg.block_width > 0 ? g.cfg.block_width : std::min(256, std::max(8, (int)(1u << (32 - __builtin_clz((unsigned)std::max(count, 8) - 1)))));
+  int B = g.cfg.block_width;
+  if (B <= 0) {
+    // the next power of two that holds the requests, within [8, 256]; with
+    // cfg.autotune, no wider than the tuned width of this graph and storage
+    B = std::min(256, std::max(8, (int)(1u << (32 - __builtin_clz((unsigned)std::max(count, 8) - 1)))));
+    if (g.cfg.autotune) B = std::min(B, tuned_width(g, g.cfg.storage, {}, nullptr));
+  }
   BatchCache* bc = static_cast<BatchCache*>(g.batch);
   if (!bc) {
     bc = new BatchCache();
@@ -1389,6 +1399,103 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
     }
     eng.flush_profile();
   }
+}
+
+// ------------------------------------------------------------------ autotune
+
+namespace {
+struct TuneKey {
+  uint64_t digest;
+  int storage, device;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(digest, storage, device) < std::tie(o.digest, o.storage, o.device);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, double>> g_tune;  // width, us per column-pass
+
+// Mean device time (ms) of `reps` passes of one engine at a forced storage stage.
+double time_passes(ColumnEngine& eng, int stage, int reps, cudaStream_t st) {
+  eng.pass(stage);  // warm-up (first launch of this instance)
+  cudaEvent_t e0, e1;
+  GP_CUDA_TRY(cudaEventCreate(&e0));
+  GP_CUDA_TRY(cudaEventCreate(&e1));
+  GP_CUDA_TRY(cudaEventRecord(e0, st));
+  for (int i = 0; i < reps; ++i) eng.pass(stage);
+  GP_CUDA_TRY(cudaEventRecord(e1, st));
+  GP_CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / reps;
+}
+}  // namespace
+
+// Time the column engine at each candidate width on this graph (every column
+// a fixed-K query from a distinct non-isolated node, so nothing retires), and
+// return the width with the least device time per column and pass.  With
+// 16-bit storage a block spends about its first half in the FP32 warm-up, so
+// the cost is 0.45 of an FP32 pass plus 0.55 of a 16-bit one.
+int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_out) {
+  int dev = 0;
+  GP_CUDA_TRY(cudaGetDevice(&dev));
+  const TuneKey key{g.digest, (int)storage, dev};
+  const bool custom = !widths.empty();
+  if (!custom) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      if (us_out) *us_out = it->second.second;
+      return it->second.first;
+    }
+    widths = {32, 64, 128, 256};
+  }
+  std::vector<int32_t> srcs;
+  for (int64_t u = 0; u < g.n && (int)srcs.size() < 256; ++u)
+    if (g.h_deg[u] > 0) srcs.push_back((int32_t)u);
+  GP_REQUIRE(!srcs.empty(), "the graph has no edges");
+  int best = 0;
+  double best_us = 0.0;
+  for (int B : widths) {
+    GP_REQUIRE(B >= 8 && B <= 256 && (B & (B - 1)) == 0, "widths must be powers of two in [8, 256]");
+    size_t free_b = 0, total_b = 0;
+    GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    if ((size_t)B * ColumnEngine::bytes_per_column(g, storage) > free_b / 2) continue;
+    ColumnEngine eng(g, B, storage, g.stream);
+    std::vector<gp_request> reqs(B);
+    std::vector<uint64_t> tags(B);
+    for (int j = 0; j < B; ++j) {
+      gp_request r{};
+      r.function = GP_FN_PPR;
+      r.source = srcs[j % srcs.size()];
+      r.param = 0.2;
+      r.l1_tol = 1e-6;
+      r.k_rule = GP_K_FIXED;
+      r.k_fixed = g.cfg.k_max - 1;  // never retires while timed
+      r.out_dtype = GP_F64;
+      r.y_on_device = 1;
+      r.y_out = nullptr;  // never collected
+      reqs[j] = r;
+      tags[j] = (uint64_t)j;
+    }
+    eng.restart();
+    eng.admit(reqs, tags);
+    const double t32 = time_passes(eng, 0, 2, g.stream);
+    const double ms = storage == GP_F32 ? t32 : 0.45 * t32 + 0.55 * time_passes(eng, 3, 2, g.stream);
+    const double us = 1000.0 * ms / B;
+    if (best == 0 || us < best_us) {
+      best = B;
+      best_us = us;
+    }
+  }
+  GP_REQUIRE(best > 0, "no candidate width fits in device memory");
+  if (!custom) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {best, best_us};
+  }
+  if (us_out) *us_out = best_us;
+  return best;
 }
 
 void free_batch_work(Graph& g) {

@@ -65,8 +65,9 @@ class ColumnEngine {
   // Put requests into free columns (isolated sources are answered at once and
   // take no column).  Returns the column of each request (-1: answered).
   std::vector<int> admit(const std::vector<gp_request>& reqs, std::vector<uint64_t> tags);
-  // One fused pass: stop rule and coefficients, then the SpMM step.
-  void pass();
+  // One fused pass: stop rule and coefficients, then the SpMM step
+  // (force_stage >= 0 fixes the storage stage: timing only).
+  void pass(int force_stage = -1);
   // Write the outputs of the columns whose rule fired (all busy columns when
   // force_all), free them, and report them.
   std::vector<Finished> collect(bool force_all);

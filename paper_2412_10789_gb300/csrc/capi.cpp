@@ -146,6 +146,22 @@ extern "C" gp_status gp_poll(gp_graph* gh, uint64_t ticket, gp_query_info* info)
   return rc != GP_OK ? rc : st;
 }
 
+extern "C" gp_status gp_autotune(gp_graph* gh, gp_dtype storage, const int32_t* widths, int32_t nwidths,
+                                  int32_t* best_width, double* us_per_column_pass) {
+  return guard([&] {
+    Graph* g = as_graph(gh);
+    GP_REQUIRE(best_width, "best_width is NULL");
+    GP_REQUIRE(storage == GP_F32 || storage == GP_BF16 || storage == GP_F16, "storage must be GP_F32, GP_BF16 or GP_F16");
+    GP_REQUIRE(nwidths >= 0 && (nwidths == 0 || widths), "widths is NULL");
+    std::vector<int> w(widths, widths + nwidths);
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    double us = 0.0;
+    const int b = tuned_width(*g, storage, w, &us);
+    *best_width = b;
+    if (us_per_column_pass) *us_per_column_pass = us;
+  });
+}
+
 extern "C" gp_status gp_serve_stats(gp_graph* gh, uint64_t* completed, uint64_t* steps, double* mean_active) {
   return guard([&] { serve_stats(*as_graph(gh), completed, steps, mean_active); });
 }

@@ -138,6 +138,7 @@ struct QueryWork {
 
 struct Graph {
   int64_t n = 0, nnz = 0, n_active = 0, max_degree = 0;
+  uint64_t digest = 0;        // FNV-1a of n, nnz and the degree sequence (autotune cache key)
   bool rp64 = false;          // row_ptr stored as int64
   void* rp = nullptr;         // relabelled row_ptr (int32 or int64), device
   int32_t* ci = nullptr;      // relabelled col_idx, device
@@ -182,6 +183,9 @@ void free_query_work(Graph& g);
 
 // batch.cu / serve.cu
 void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos);
+// Block width with the least device time per column and pass on this graph
+// (cached per graph digest, storage and device unless widths are given).
+int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_per_column_pass);
 void free_batch_work(Graph& g);
 uint64_t serve_submit(Graph& g, const gp_request& req);
 gp_status serve_poll(Graph& g, uint64_t ticket, gp_query_info* info);

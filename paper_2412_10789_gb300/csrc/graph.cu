@@ -248,6 +248,19 @@ void ingest(Graph& g, const void* row_ptr_in, int in_rp64, const int32_t* col_id
   GP_CUDA_TRY(cudaStreamSynchronize(st));
   g.h_newid.swap(newid);
   g.h_deg.swap(deg);
+  {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a
+    auto mix = [&](uint64_t v) {
+      for (int i = 0; i < 8; ++i) {
+        h ^= (v >> (8 * i)) & 0xff;
+        h *= 1099511628211ull;
+      }
+    };
+    mix((uint64_t)n);
+    mix((uint64_t)g.nnz);
+    for (int32_t d : g.h_deg) mix((uint64_t)(uint32_t)d);
+    g.digest = h;
+  }
   build_schedule(g, nrp);
   g.h_rp_relabelled.swap(nrp);
 }

@@ -123,6 +123,8 @@ def load_library():
             "gp_poll": (ctypes.c_int, [vp, u64, pinfo]),
             "gp_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                               ctypes.POINTER(dbl)]),
+            "gp_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(i32), i32, ctypes.POINTER(i32),
+                                           ctypes.POINTER(dbl)]),
             "gp_launch_count": (u64, []),
             "gp_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
             "gp_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(dbl)]),
@@ -203,6 +205,7 @@ class Graph:
         n, nnz, na, md = (ctypes.c_int64() for _ in range(4))
         _check(_lib.gp_graph_info(handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(na), ctypes.byref(md)))
         self.n, self.nnz, self.n_active, self.max_degree = n.value, nnz.value, na.value, md.value
+        self.storage = GP_F32
 
     def close(self):
         if self.handle:
@@ -260,7 +263,9 @@ def gp_graph_create(n, row_ptr, col_idx, degree, cfg=None, use_torch_memory=True
     _check(lib.gp_graph_create(int(n), nnz, rp_ptr, rp64, ci_ptr, dg_ptr, rp_dev, ctypes.byref(cfg),
                                ctypes.byref(h)))
     keep.append(cfg)
-    return Graph(h, keep)
+    g = Graph(h, keep)
+    g.storage = int(cfg.storage)
+    return g
 
 
 def gp_graph_destroy(g: Graph):
@@ -364,6 +369,17 @@ def gp_launch_count() -> int:
 
 def gp_profile_enable(g: Graph, on: bool = True):
     _check(_lib.gp_profile_enable(g.handle, 1 if on else 0))
+
+
+def gp_autotune(g: Graph, storage=None, widths=None):
+    """Block width with the least device time per column and pass on this graph."""
+    lib = load_library()
+    st = g.storage if storage is None else storage
+    arr = (ctypes.c_int32 * len(widths))(*widths) if widths else None
+    best, us = ctypes.c_int32(), ctypes.c_double()
+    _check(lib.gp_autotune(g.handle, int(st), arr, len(widths) if widths else 0, ctypes.byref(best),
+                           ctypes.byref(us)))
+    return {"width": best.value, "us_per_column_pass": us.value}
 
 
 def gp_profile_read(g: Graph):

@@ -235,3 +235,32 @@ def test_batch_profile_counts_passes(gp):
         assert prof["step_bytes"] >= prof["step_launches"] * per_pass_min
     finally:
         dg.close()
+
+
+def test_autotune_picks_a_candidate_and_batches_with_it(gp):
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=gp.GP_BF16, autotune=1)
+    try:
+        r = gp.gp_autotune(dg, widths=[16, 32, 64])
+        assert r["width"] in (16, 32, 64) and r["us_per_column_pass"] > 0.0
+        d = gp.gp_autotune(dg)  # default candidates: measured once, then cached per graph structure
+        assert d["width"] in (32, 64, 128, 256)
+        assert gp.gp_autotune(dg) == d
+        # another handle on the same graph structure reuses the cached choice
+        dg2 = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=gp.GP_BF16, autotune=1)
+        try:
+            assert gp.gp_autotune(dg2) == d
+        finally:
+            dg2.close()
+        # gp_batch with block_width 0 and autotune runs at the tuned width and stays accurate
+        srcs = gg.sources(g, 10, 41)
+        ys = _outputs(g, len(srcs))
+        infos = gp.gp_batch(dg, _requests(gp, g, srcs, 1e-4, ys))
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            l1 = O.errors(g, O.chebypower(g, int(s), KINDS[fn], p, 150), ys[i].cpu().numpy())["l1"]
+            assert l1 <= 1e-4, (i, l1, infos[i])
+        with pytest.raises(Exception):
+            gp.gp_autotune(dg, widths=[48])  # not a power of two
+    finally:
+        dg.close()
