@@ -98,14 +98,17 @@ void or_cheb_coeffs(int kind, double param, int K, int M, double* c) {
 static double deg_of(const int64_t* row_ptr, int64_t u) { return (double)(row_ptr[u + 1] - row_ptr[u]); }
 
 /* y = P x with P = A D^{-1}:  y(u) = sum_{v in N(u)} A_uv x(v) / d_v.
- * Every v listed in row u has d_v >= 1 (the adjacency is symmetric).          */
+ * In a symmetric adjacency every listed v has d_v >= 1; a CSR that lists a
+ * node with an empty row (accepted only with the symmetry check off) takes
+ * 1/d_v := 0 for it, the zero column of P that a degree-0 node has.            */
 void or_P_apply(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* x, double* y) {
 #pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t u = 0; u < n; ++u) {
     double s = 0.0;
     for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
       int64_t v = col_idx[e];
-      s += x[v] / deg_of(row_ptr, v);
+      const double d = deg_of(row_ptr, v);
+      if (d > 0.0) s += x[v] / d;
     }
     y[u] = s;
   }

@@ -25,7 +25,7 @@ MUTANTS = {
     # r_{k+1} = 2 P r_k + r_{k-1}
     "sign_of_rkm1": ("2.0 * pr[u] - r", "2.0 * pr[u] + r"),
     # D^-1 A instead of A D^-1 (divide by the row's degree)
-    "row_degree": ("s += x[v] / deg_of(row_ptr, v);", "s += x[v] / deg_of(row_ptr, u);"),
+    "row_degree": ("const double d = deg_of(row_ptr, v);", "const double d = deg_of(row_ptr, u);"),
     # c_0 with 2/pi like the other coefficients
     "c0_weight": ("c[k] = (k == 0 ? 1.0 : 2.0) / OR_PI * integral;", "c[k] = 2.0 / OR_PI * integral;"),
     # the last term c_K r_K dropped

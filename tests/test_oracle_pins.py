@@ -220,6 +220,16 @@ def test_isolated_source():
         assert np.max(np.abs(O.dense_gp(g, 5, kind, param) - want)) < 1e-14
 
 
+def test_degree_zero_column_is_zero():
+    # Reading 1/d := 0 on a CSR that lists a node with an empty row (asymmetric,
+    # accepted only with the symmetry check off).  Rows 0 -> {1, 2}, 1 -> {0},
+    # 2 -> {}: d = (2, 1, 0) and P = A D^-1 = [[0, 1, 0], [1/2, 0, 0], [0, 0, 0]].
+    g = gg.Graph("asym3", 3, np.array([0, 2, 3, 3], dtype=np.int64), np.array([1, 2, 0], dtype=np.int32))
+    x = np.array([0.75, -1.5, 4.0])
+    assert np.array_equal(O.P_apply(g, x), np.array([-1.5, 0.375, 0.0]))
+    assert np.array_equal(O.P_apply(g, np.array([0.0, 0.0, 1.0])), np.zeros(3))
+
+
 def test_stopping_rule_meets_l1():
     # The l1 stopping reading stops where tail(K) * max_l ||r_l||_1 <= tol, which bounds
     # ||y - y_K||_1 by the triangle inequality as long as later ||r_k||_1 stay below the max.
