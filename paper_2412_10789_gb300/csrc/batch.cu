@@ -284,6 +284,7 @@ struct SpmmArgs {
   int64_t na;           // rows of the blocks (nodes with degree >= 1)
   int B;                // columns of this pass (a prefix of each row)
   int ldb;              // row stride of the blocks, in elements
+  int check;            // col_idx lists rows beyond the active ones (host: picks the kernel)
 };
 
 // Combine the entry groups' partial sums (lanes cg, cg + CG, cg + 2 CG, ...).
@@ -305,7 +306,6 @@ struct Geo {
   static constexpr int OP = LC * sP / SB;         // rounds of the own Q_{k-1} segment (1 or 2)
   static constexpr int OY = LC * 4 / SB;          // rounds of the own y segment (1 or 2)
   static constexpr int OWN = OP + OY;
-  static constexpr int PW = SB / 4;               // floats per round of an FP32 segment
   static constexpr uint32_t kStride = 32 * SB;    // ring bytes per round (whole warp)
   static constexpr uint32_t kMask = S * kStride - 1;
   static_assert(S >= 2 && (S & (S - 1)) == 0, "ring depth must be a power of two");
@@ -331,10 +331,13 @@ struct Lane {
   int cg, g, CG, EG, lane;
 };
 
-// Source of the gathered segment of neighbour v (rows beyond the active ones,
-// which only an unvalidated asymmetric CSR can list, read zeros).
+// Source of the gathered segment of neighbour v.  Rows beyond the active ones,
+// which only an unvalidated asymmetric CSR can list, read zeros; the check is
+// compiled in only for graphs whose ingest found such entries (CHECK).
+template <bool CHECK>
 __device__ __forceinline__ const unsigned char* gather_src(const Lane& L, int v) {
-  return v < L.na ? L.qseg + (uint64_t)(uint32_t)v * L.rowG : L.zero;
+  if constexpr (CHECK) return v < L.na ? L.qseg + (uint64_t)(uint32_t)v * L.rowG : L.zero;
+  return L.qseg + (uint64_t)(uint32_t)v * L.rowG;
 }
 
 // Source of piece o (SB bytes) of row u's own Q_{k-1} segment (o < OP) or y
@@ -459,7 +462,7 @@ __device__ __forceinline__ void own_round(const Lane& L, int64_t u, float d, int
 // gather rounds, then OP rounds of its Q_{k-1} segment and OY of its y
 // segment.  The caller has issued the next tile's index copies, which join
 // round 0's copy group.
-template <typename TG, typename TP, typename TO, int LC>
+template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
   constexpr int S = C::S, SB = C::SB, OP = C::OP, OWN = C::OWN;
@@ -474,7 +477,7 @@ __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& 
     if (p_seq < nseq) {
       const uint32_t dst = L.ring + p_off;
       if (p_left > 0) {
-        if (p_row < nrows) cp_seg<SB>(dst, gather_src(L, *p_ci));
+        if (p_row < nrows) cp_seg<SB>(dst, gather_src<CHECK>(L, *p_ci));
         ++p_ci;
         --p_left;
       } else {
@@ -581,7 +584,7 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
 // each row's entries (entry j of a row goes to group j % EG) and combine their
 // sums by shuffles; kind 1 rows then take OP + OY own rounds (group 0), a
 // chunk publishes its partial and the last chunk of the row updates it.
-template <typename TG, typename TP, typename TO, int LC, bool CHUNK>
+template <typename TG, typename TP, typename TO, int LC, bool CHUNK, bool CHECK>
 __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
   constexpr int S = C::S, SB = C::SB, OP = C::OP, OWN = C::OWN;
@@ -598,7 +601,7 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
     if (p_seq < nseq) {
       const uint32_t dst = L.ring + p_off;
       if (p_left > 0) {
-        if (p_j < d) cp_seg<SB>(dst, gather_src(L, *p_ci));
+        if (p_j < d) cp_seg<SB>(dst, gather_src<CHECK>(L, *p_ci));
         p_ci += EG;
         p_j += EG;
         if (--p_left == 0 && CHUNK) ++p_seq;
@@ -677,7 +680,7 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
 // lane group's round copies either one gathered neighbour row segment of
 // Q_k, or one piece of its own row's Q_{k-1} and y (fetched through the same
 // ring, after the row's gathers, so the update finds them on chip).
-template <typename TG, typename TP, typename TO, int LC>
+template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __grid_constant__ SpmmArgs a) {
   using C = Geo<TG, TP, TO, LC>;
   extern __shared__ __align__(16) unsigned char s_raw[];
@@ -738,11 +741,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
     int4 nd2 = make_int4(0, 0, 0, 0);
     if (w + 2 * nwarps < a.ntiles) nd2 = a.tiles[w + 2 * nwarps];
     if (t.kind == 0)
-      tile_rows_per_group<TG, TP, TO, LC>(L, t, ci_t, nrm);
+      tile_rows_per_group<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
     else if (t.kind == 1)
-      tile_rows_per_warp<TG, TP, TO, LC, false>(L, t, ci_t, nrm);
+      tile_rows_per_warp<TG, TP, TO, LC, false, CHECK>(L, t, ci_t, nrm);
     else
-      tile_rows_per_warp<TG, TP, TO, LC, true>(L, t, ci_t, nrm);
+      tile_rows_per_warp<TG, TP, TO, LC, true, CHECK>(L, t, ci_t, nrm);
     cur = nd;
     nd = nd2;
     bwait<0>();  // only empty groups remain; the next tile restarts the ring at slot 0
@@ -898,13 +901,21 @@ int device_sms() {
   return sms > 0 ? sms : 1;
 }
 
-template <typename TG, typename TP, typename TO, int LC>
-void launch_spmm_lc(const SpmmArgs& a, cudaStream_t st) {
-  static const cudaError_t attr = cudaFuncSetAttribute(spmm_step_kernel<TG, TP, TO, LC>,
+template <typename TG, typename TP, typename TO, int LC, bool CHECK>
+void launch_spmm_k(const SpmmArgs& a, cudaStream_t st) {
+  static const cudaError_t attr = cudaFuncSetAttribute(spmm_step_kernel<TG, TP, TO, LC, CHECK>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmSmem);
   GP_CUDA_TRY(attr);
-  spmm_step_kernel<TG, TP, TO, LC><<<device_sms(), kBatchThreads, kSpmmSmem, st>>>(a);
+  spmm_step_kernel<TG, TP, TO, LC, CHECK><<<device_sms(), kBatchThreads, kSpmmSmem, st>>>(a);
   GP_LAUNCHED();
+}
+
+template <typename TG, typename TP, typename TO, int LC>
+void launch_spmm_lc(const SpmmArgs& a, cudaStream_t st) {
+  if (a.check)
+    launch_spmm_k<TG, TP, TO, LC, true>(a, st);
+  else
+    launch_spmm_k<TG, TP, TO, LC, false>(a, st);
 }
 
 // With 16-bit gathers a lane owns 16 columns (32 bytes per round) when
@@ -1197,6 +1208,7 @@ void ColumnEngine::pass(int force_stage) {
   a.na = g_.n_active;
   a.B = bw_;
   a.ldb = B_;
+  a.check = g_.ci_beyond_active ? 1 : 0;
   const bool prof = profile_;
   if (prof) {
     while (events_.size() < prof_marks_.size() * 2 + 2) {

@@ -140,6 +140,7 @@ struct Graph {
   int64_t n = 0, nnz = 0, n_active = 0, max_degree = 0;
   uint64_t digest = 0;        // FNV-1a of n, nnz and the degree sequence (autotune cache key)
   bool rp64 = false;          // row_ptr stored as int64
+  bool ci_beyond_active = false;  // some col_idx entry names an isolated node (asymmetric input)
   void* rp = nullptr;         // relabelled row_ptr (int32 or int64), device
   int32_t* ci = nullptr;      // relabelled col_idx, device
   int32_t* order = nullptr;   // order[i] = caller id of relabelled row i, device

@@ -85,18 +85,27 @@ __global__ void validate_rows_kernel(int64_t n, const RP* __restrict__ rp, const
 }
 
 // new_ci[new_rp[i] + j] = newid[ci[rp[order[i]] + j]]  (one warp per new row)
+// (*beyond is set when an entry names a node of degree 0, i.e. a relabelled
+// id >= n_active: possible only for an unvalidated asymmetric CSR.)
 template <typename RP>
 __global__ void renumber_kernel(int64_t n, const RP* __restrict__ rp, const int32_t* __restrict__ ci,
                                 const RP* __restrict__ new_rp, const int32_t* __restrict__ order,
-                                const int32_t* __restrict__ newid, int32_t* __restrict__ new_ci) {
+                                const int32_t* __restrict__ newid, int32_t* __restrict__ new_ci,
+                                int64_t n_active, int* beyond) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  bool far = false;
   for (int64_t i = warp; i < n; i += nwarps) {
     int64_t u = order[i];
     int64_t src = rp[u], dst = new_rp[i], d = new_rp[i + 1] - dst;
-    for (int64_t j = lane; j < d; j += 32) new_ci[dst + j] = newid[ci[src + j]];
+    for (int64_t j = lane; j < d; j += 32) {
+      const int32_t v = newid[ci[src + j]];
+      new_ci[dst + j] = v;
+      far |= v >= n_active;
+    }
   }
+  if (far) *beyond = 1;
 }
 
 // Inverse of renumber_kernel: rows back to the caller's numbering.
@@ -243,9 +252,15 @@ void ingest(Graph& g, const void* row_ptr_in, int in_rp64, const int32_t* col_id
     throw Error{GP_EINVAL, "invalid CSR at row " + std::to_string(res[0]) + ":" + what};
   }
   // ---- renumber columns into the relabelled CSR
-  renumber_kernel<RP><<<grid, 256, 0, st>>>(n, orp.p, ci_src, (const RP*)g.rp, g.order, g.newid, g.ci);
+  Tmp<int> beyond(A, 1);
+  GP_CUDA_TRY(cudaMemsetAsync(beyond.p, 0, sizeof(int), st));
+  renumber_kernel<RP><<<grid, 256, 0, st>>>(n, orp.p, ci_src, (const RP*)g.rp, g.order, g.newid, g.ci,
+                                            g.n_active, beyond.p);
   GP_LAUNCHED();
+  int h_beyond = 0;
+  GP_CUDA_TRY(cudaMemcpyAsync(&h_beyond, beyond.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   GP_CUDA_TRY(cudaStreamSynchronize(st));
+  g.ci_beyond_active = h_beyond != 0;
   g.h_newid.swap(newid);
   g.h_deg.swap(deg);
   {

@@ -264,3 +264,33 @@ def test_autotune_picks_a_candidate_and_batches_with_it(gp):
             gp.gp_autotune(dg, widths=[48])  # not a power of two
     finally:
         dg.close()
+
+
+def test_batch_unvalidated_asymmetric_csr(gp):
+    """A CSR whose rows list nodes of degree 0 (asymmetric, symmetry check off):
+    those neighbours contribute 0 (1/d := 0), in the batched kernel as in the
+    oracle, through the kernel variant that checks gathered rows."""
+    base = gg.rmat(10, 8, seed=5)
+    rows = [list(base.col_idx[base.row_ptr[u]:base.row_ptr[u + 1]]) for u in range(base.n)]
+    iso = [u for u in range(base.n) if not rows[u]]
+    assert len(iso) >= 3
+    for k, u in enumerate([u for u in range(base.n) if rows[u]][:40]):
+        rows[u] = sorted(set(rows[u]) | {iso[k % len(iso)]})
+    rp = np.zeros(base.n + 1, dtype=np.int64)
+    for u in range(base.n):
+        rp[u + 1] = rp[u] + len(rows[u])
+    ci = np.array([v for r in rows for v in r], dtype=np.int32)
+    g = gg.Graph("rmat10_with_isolated_targets", base.n, rp, ci)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16, validate_symmetry=0)
+    try:
+        srcs = [u for u in range(g.n) if g.degree[u] > 0][:6]
+        ys = _outputs(g, len(srcs))
+        K = 14
+        reqs = [gp.make_request(0, int(s), 0.2, 1e-6, ys[i], k_rule=gp.GP_K_FIXED, k_fixed=K)
+                for i, s in enumerate(srcs)]
+        gp.gp_batch(dg, reqs)
+        for i, s in enumerate(srcs):
+            e = O.errors(g, O.chebypower(g, int(s), "ppr", 0.2, K), ys[i].cpu().numpy())
+            assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7, (i, e)
+    finally:
+        dg.close()
