@@ -580,20 +580,90 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
   }
 }
 
-// Kind 1 (CHUNK false) and kind 2 (CHUNK true) tiles: the EG lane groups split
-// each row's entries (entry j of a row goes to group j % EG) and combine their
-// sums by shuffles; kind 1 rows then take OP + OY own rounds (group 0), a
-// chunk publishes its partial and the last chunk of the row updates it.
-template <typename TG, typename TP, typename TO, int LC, bool CHUNK, bool CHECK>
+// A chunk's neighbour sums are complete: publish its partial; the warp that
+// publishes the row's last chunk finishes the row.
+template <typename TG, typename TP, typename TO, int LC>
+__device__ __forceinline__ void publish_chunk(const Lane& L, const BTile& t, float acc[LC], float nrm[LC]) {
+  const SpmmArgs& a = *L.a;
+  reduce_groups<LC>(acc, L.CG);
+  Store<TG>::template finish<LC>(acc);
+  const int64_t row = t.row0;
+  const int slot0 = a.poff[row], np = a.poff[row + 1] - slot0;
+  if (L.g == 0) {
+    float4* dst = reinterpret_cast<float4*>(a.part + (int64_t)(slot0 + t.a) * a.B + L.cg * LC);
+#pragma unroll
+    for (int i = 0; i < LC / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+  }
+  __threadfence();
+  __syncwarp();
+  int old = 0;
+  if (L.lane == 0) old = atomicAdd(&a.cnt[row], 1);
+  old = __shfl_sync(0xffffffffu, old, 0);
+  if (old == np - 1) finish_long_row<TP, TO, LC>(L, row, slot0, np, nrm);
+}
+
+// Kind 2 tile (a chunk of a long row): pure gather rounds, entry j = r*EG + g
+// of the chunk in round r, two rounds per iteration under one wait.
+template <typename TG, typename TP, typename TO, int LC, bool CHECK>
+__device__ __forceinline__ void tile_chunk(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
+  using C = Geo<TG, TP, TO, LC>;
+  constexpr int S = C::S, SB = C::SB;
+  static_assert(S >= 3, "two rounds per wait need at least three in the ring");
+  const int EG = L.EG, g = L.g;
+  const int len = t.b;
+  const int G = (len + EG - 1) / EG;
+  int pj = g;         // chunk entry of the next round to issue
+  uint32_t p_off = 0;
+  auto issue = [&]() {
+    if (pj < len) cp_seg<SB>(L.ring + p_off, gather_src<CHECK>(L, ci_t[pj]));
+    pj += EG;
+    p_off = (p_off + C::kStride) & C::kMask;
+  };
+  float acc[LC];
+#pragma unroll
+  for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+#pragma unroll 1
+  for (int i = 0; i < S - 1; ++i) {
+    issue();
+    bcommit();
+  }
+  int rc = 0, cj = g;
+  uint32_t c_off = 0;
+#pragma unroll 1
+  for (; rc + 1 < G; rc += 2) {
+    bwait<S - 3>();  // rounds rc and rc + 1 have landed
+    const unsigned char* s0 = L.ring_p + c_off;
+    const unsigned char* s1 = L.ring_p + ((c_off + C::kStride) & C::kMask);
+    if (cj < len) add_seg<TG, LC>(s0, acc);
+    if (cj + EG < len) add_seg<TG, LC>(s1, acc);
+    cj += 2 * EG;
+    c_off = (c_off + 2 * C::kStride) & C::kMask;
+    issue();
+    bcommit();
+    issue();
+    bcommit();
+  }
+  if (rc < G) {
+    bwait<S - 2>();
+    if (cj < len) add_seg<TG, LC>(L.ring_p + c_off, acc);
+    issue();
+    bcommit();
+  }
+  publish_chunk<TG, TP, TO, LC>(L, t, acc, nrm);
+}
+
+// Kind 1 tile: the EG lane groups split each row's entries (entry j of a row
+// goes to group j % EG) and combine their sums by shuffles; the row then takes
+// OP + OY own rounds (group 0).
+template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
   constexpr int S = C::S, SB = C::SB, OP = C::OP, OWN = C::OWN;
-  const SpmmArgs& a = *L.a;
   const int EG = L.EG, g = L.g;
-  const int d = t.b;  // entries per row (kind 1) or of the chunk (kind 2)
+  const int d = t.b;  // entries per row
   const int G = (d + EG - 1) / EG;
-  const int nseq = CHUNK ? 1 : t.a;
-  const int R = nseq * (CHUNK ? G : G + OWN);
+  const int nseq = t.a;
+  const int R = nseq * (G + OWN);
   int p_seq = 0, p_left = G, p_own = 0, p_j = g;
   const int* p_ci = ci_t + g;
   uint32_t p_off = 0;
@@ -604,7 +674,7 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
         if (p_j < d) cp_seg<SB>(dst, gather_src<CHECK>(L, *p_ci));
         p_ci += EG;
         p_j += EG;
-        if (--p_left == 0 && CHUNK) ++p_seq;
+        --p_left;
       } else {
         if (g == 0) cp_seg<SB>(dst, own_src<SB, OP>(L, t.row0 + p_seq, p_own));
         if (++p_own == OWN) {
@@ -635,25 +705,8 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
     if (c_left > 0) {
       if (c_j < d) add_seg<TG, LC>(src, acc);
       c_j += EG;
-      if (--c_left == 0 && CHUNK) {
-        // chunk done: publish its partial; the last chunk of the row finishes it
-        reduce_groups<LC>(acc, L.CG);
-        Store<TG>::template finish<LC>(acc);
-        const int64_t row = t.row0;
-        const int slot0 = a.poff[row], np = a.poff[row + 1] - slot0;
-        if (g == 0) {
-          float4* dst = reinterpret_cast<float4*>(a.part + (int64_t)(slot0 + t.a) * a.B + L.cg * LC);
-#pragma unroll
-          for (int i = 0; i < LC / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
-        }
-        __threadfence();
-        __syncwarp();
-        int old = 0;
-        if (L.lane == 0) old = atomicAdd(&a.cnt[row], 1);
-        old = __shfl_sync(0xffffffffu, old, 0);
-        if (old == np - 1) finish_long_row<TP, TO, LC>(L, row, slot0, np, nrm);
-      }
-    } else if (!CHUNK) {
+      --c_left;
+    } else {
       if (c_own == 0) {  // the row's sums, before its first own piece
         reduce_groups<LC>(acc, L.CG);
         Store<TG>::template finish<LC>(acc);
@@ -743,9 +796,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
     if (t.kind == 0)
       tile_rows_per_group<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
     else if (t.kind == 1)
-      tile_rows_per_warp<TG, TP, TO, LC, false, CHECK>(L, t, ci_t, nrm);
+      tile_rows_per_warp<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
     else
-      tile_rows_per_warp<TG, TP, TO, LC, true, CHECK>(L, t, ci_t, nrm);
+      tile_chunk<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
     cur = nd;
     nd = nd2;
     bwait<0>();  // only empty groups remain; the next tile restarts the ring at slot 0
