@@ -64,9 +64,12 @@ constexpr float kF16Scale = 4096.0f;
 //           chunk order and updates the row.
 // Descriptor int4 {row0, e0 low, e0 high, meta}: meta bits 0-1 kind,
 // bits 2-16 nrows (kinds 0, 1) or p (kind 2), bits 17-31 d or len.
-constexpr int kBTileCap = 508;   // entries of a tile (room for 16-byte alignment in kBTileSpan)
-constexpr int kBTileSpan = 512;  // staged indices per buffer
-constexpr int kBTileCost = 512;  // rows tiles: nrows * (d + 3) at most
+#ifndef GP_SPMM_TILE
+#define GP_SPMM_TILE 512
+#endif
+constexpr int kBTileSpan = GP_SPMM_TILE;      // staged indices per buffer
+constexpr int kBTileCap = kBTileSpan - 4;     // entries of a tile (room for 16-byte alignment)
+constexpr int kBTileCost = kBTileSpan;        // rows tiles: nrows * (d + 3) at most
 #ifndef GP_SPMM_THREADS
 #define GP_SPMM_THREADS 512
 #endif
@@ -285,6 +288,7 @@ struct SpmmArgs {
   int B;                // columns of this pass (a prefix of each row)
   int ldb;              // row stride of the blocks, in elements
   int check;            // col_idx lists rows beyond the active ones (host: picks the kernel)
+  int* tile_ctr;        // tiles claimed past the first two per warp (zeroed by the control kernel)
 };
 
 // Combine the entry groups' partial sums (lanes cg, cg + CG, cg + 2 CG, ...).
@@ -772,8 +776,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
 #pragma unroll
   for (int i = 0; i < LC; ++i) nrm[i] = 0.f;
 
+  // Tiles: each warp starts with tiles w and w + nwarps, then takes the next
+  // unclaimed tile from a per-pass counter one tile ahead, so the pass ends
+  // when the work does rather than with the warp that drew the costliest tiles.
   const int64_t nwarps = (int64_t)gridDim.x * kBatchWarps;
   int64_t w = (int64_t)blockIdx.x * kBatchWarps + warp;
+  int64_t wn = w + nwarps;
   int4 cur = make_int4(0, 0, 0, 0), nd = make_int4(0, 0, 0, 0);
   if (w < a.ntiles) {
     cur = a.tiles[w];
@@ -781,18 +789,21 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
     stage_indices(s_ci, a.ci, t0.e0, tile_len(t0), lane);
     bcommit();
     bwait<0>();
-    if (w + nwarps < a.ntiles) nd = a.tiles[w + nwarps];
+    if (wn < a.ntiles) nd = a.tiles[wn];
   }
-  for (int buf = 0; w < a.ntiles; w += nwarps, buf ^= 1) {
+  for (int buf = 0; w < a.ntiles; buf ^= 1) {
     __syncwarp();  // this tile's staged indices are visible; the other buffer is free
     const BTile t = decode_btile(cur);
     const int* ci_t = s_ci + buf * kBTileSpan + (int)(t.e0 & 3);
-    if (w + nwarps < a.ntiles) {  // the next tile's indices join this tile's first copy group
+    if (wn < a.ntiles) {  // the next tile's indices join this tile's first copy group
       const BTile tn = decode_btile(nd);
       stage_indices(s_ci + (buf ^ 1) * kBTileSpan, a.ci, tn.e0, tile_len(tn), lane);
     }
+    int64_t wnn = 0;
+    if (lane == 0) wnn = 2 * nwarps + atomicAdd(a.tile_ctr, 1);
+    wnn = __shfl_sync(0xffffffffu, wnn, 0);
     int4 nd2 = make_int4(0, 0, 0, 0);
-    if (w + 2 * nwarps < a.ntiles) nd2 = a.tiles[w + 2 * nwarps];
+    if (wnn < a.ntiles) nd2 = a.tiles[wnn];
     if (t.kind == 0)
       tile_rows_per_group<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
     else if (t.kind == 1)
@@ -801,6 +812,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
       tile_chunk<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
     cur = nd;
     nd = nd2;
+    w = wn;
+    wn = wnn;
     bwait<0>();  // only empty groups remain; the next tile restarts the ring at slot 0
   }
 #pragma unroll
@@ -813,8 +826,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
 
 // Before each pass: fold the last pass's norm into each active column's
 // running max, apply its stop rule, and set the coefficient of the next step.
-__global__ void control_kernel(ColState* col, const ColParam* par, ColStat* stat, float* norm, int B, int kcap) {
+__global__ void control_kernel(ColState* col, const ColParam* par, ColStat* stat, float* norm, int B, int kcap,
+                               int* tile_ctr) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) *tile_ctr = 0;
   if (j >= B) return;
   ColState& cs = col[j];
   const ColParam& p = par[j];
@@ -1060,6 +1075,7 @@ ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st)
     part_ = (float*)A.get(sizeof(float) * (size_t)std::max(poff.back(), 1) * B);
     cnt_ = (int*)A.get(sizeof(int) * std::max(nlong_, 1));
     zero_ = A.get(sizeof(float) * B);
+    tile_ctr_ = (int*)A.get(sizeof(int) * 4);
     if (!tiles.empty())
       GP_CUDA_TRY(cudaMemcpyAsync(tiles_, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, st_));
     GP_CUDA_TRY(cudaMemcpyAsync(poff_, poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice, st_));
@@ -1088,7 +1104,7 @@ void ColumnEngine::release() {
   Allocator& A = g_.alloc;
   for (void* p : {(void*)f_[0], (void*)f_[1], h_[0], h_[1], (void*)y_, (void*)col_, (void*)par_, (void*)stat_,
                   (void*)norm_, (void*)scratch_, outs_, stage_, (void*)tiles_, (void*)poff_, (void*)ldeg_,
-                  (void*)part_, (void*)cnt_, zero_})
+                  (void*)part_, (void*)cnt_, zero_, (void*)tile_ctr_})
     A.put(p);
   stat_ = nullptr;
   stage_ = nullptr;
@@ -1103,6 +1119,7 @@ void ColumnEngine::release() {
   tiles_ = nullptr;
   ldeg_ = nullptr;
   zero_ = nullptr;
+  tile_ctr_ = nullptr;
   poff_ = nullptr;
   part_ = nullptr;
   cnt_ = nullptr;
@@ -1233,7 +1250,7 @@ void ColumnEngine::pass(int force_stage) {
   int w = 8;
   while (w < last + 1) w <<= 1;
   bw_ = std::min(w, B_);
-  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_);
+  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_);
   GP_LAUNCHED();
   // storage stage of this pass: FP32 until every column's warm-up has passed
   int stage = 0;
@@ -1262,6 +1279,7 @@ void ColumnEngine::pass(int force_stage) {
   a.B = bw_;
   a.ldb = B_;
   a.check = g_.ci_beyond_active ? 1 : 0;
+  a.tile_ctr = tile_ctr_;
   const bool prof = profile_;
   if (prof) {
     while (events_.size() < prof_marks_.size() * 2 + 2) {

@@ -117,6 +117,7 @@ class ColumnEngine {
   int* poff_ = nullptr;
   int64_t* ldeg_ = nullptr;   // degrees of the long (chunked) rows
   void* zero_ = nullptr;      // B zero floats
+  int* tile_ctr_ = nullptr;   // dynamic tile counter of the pass
   float* part_ = nullptr;
   int* cnt_ = nullptr;
   std::vector<Slot> slots_;
