@@ -91,8 +91,8 @@ struct DevBuf {
 //   chunk tile (meta bit 0 = 1): len = meta[1..10] entries of the long row row0,
 //              chunk index p = meta[11..31]; the warp that finishes a row's last
 //              chunk adds the chunks' partial sums in chunk order.
-// Warps take tiles round-robin (all tiles move about the same number of
-// entries), double-buffering their indices with cp.async (step.cuh).
+// Warps claim tiles from a per-pass counter (all tiles move about the same
+// number of entries), double-buffering their indices with cp.async (step.cuh).
 #ifndef GP_STEP_THREADS
 #define GP_STEP_THREADS 768
 #endif

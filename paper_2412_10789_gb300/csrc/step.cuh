@@ -10,8 +10,8 @@
 // so no r_k is read twice.
 //
 // Work: tiles of at most kTileCap consecutive col_idx entries (schedule.cpp):
-// runs of equal-degree rows, or chunks of one long row.  Warps take tiles
-// round-robin; each warp double-buffers tile indices in shared memory, copying
+// runs of equal-degree rows, or chunks of one long row.  Warps claim tiles
+// from a per-pass counter; each warp double-buffers tile indices in shared memory, copying
 // the next tile's col_idx with 16-byte cp.async while it gathers and sums the
 // current one.  Gathers of indices below `hub` read a shared-memory copy of
 // the hub rows of Q_k (the most gathered values); the rest go to L2.  The
@@ -32,7 +32,7 @@ struct StepArgs {
   float* qprev;        // Q_{k-1} in, Q_{k+1} out
   float2* y;           // y (hi, lo)
   float* norms;        // ||r_l||_1
-  int* state;          // [0] = stop K
+  int* state;          // [0] = stop K, [2 + k] = tiles claimed in pass k
   const int* poff;     // long rows: first chunk slot
   float2* part;        // long rows: chunk partial sums
   int* cnt;            // long rows: chunks finished
@@ -325,13 +325,20 @@ __global__ void __launch_bounds__(kStepThreads, 1) cheb_step_kernel(const __grid
     for (int i = threadIdx.x; i < a.hub / 4; i += kStepThreads) dst[i] = __ldcg(src + i);
   }
   __syncthreads();
+  // Each warp starts with tiles t and t + stride, then claims the next
+  // unclaimed tile from this pass's counter (state[2 + k], zeroed per query)
+  // one tile ahead, so no warp is left with a run of costly tiles at the end.
+  int64_t tn = t + stride;
   int b = 0;
-  for (; t < a.ntiles; t += stride) {
+  while (t < a.ntiles) {
     TileInfo nxt{};
-    if (t + stride < a.ntiles) {
-      nxt = decode(a.tiles[t + stride]);
+    if (tn < a.ntiles) {
+      nxt = decode(a.tiles[tn]);
       stage_indices(c, nxt, wbase + (b ^ 1) * kTileSpan);
     }
+    int64_t tnn = 0;
+    if (lane == 0) tnn = 2 * stride + atomicAdd(&a.state[2 + a.k], 1);
+    tnn = __shfl_sync(0xffffffffu, tnn, 0);
     cp_async_commit();
     cp_async_wait<1>();  // this lane's copies of tile t have landed
     __syncwarp();        // ... and every lane's
@@ -343,6 +350,8 @@ __global__ void __launch_bounds__(kStepThreads, 1) cheb_step_kernel(const __grid
     __syncwarp();  // the buffer is free for the copy two tiles ahead
     cur = nxt;
     b ^= 1;
+    t = tn;
+    tn = tnn;
   }
   cp_async_wait<0>();
   // ||r_{k+1}||_1: warp sums, block sum, one atomic per CTA
