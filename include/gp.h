@@ -182,6 +182,20 @@ gp_status gp_power(gp_graph* g, int32_t function, int32_t source, double param, 
 gp_status gp_batch(gp_graph* g, int32_t count, const gp_request* reqs, gp_query_info* infos);
 
 /*
+ * Batched queries in Clenshaw's backward form of the same truncated sum
+ * y_K = sum_{k<=K} c_k T_k(P) e_s (Lemma 1; the paper's Further Related Work
+ * cites Clenshaw's recurrence for the stability of Chebyshev sums):
+ * b_{K+1} = b_{K+2} = 0, b_k = c_k e_s + 2 P b_{k+1} - b_{k+2} for k = K..1,
+ * y = c_0 e_s + P b_1 - b_2.  K must be known before the first step, so every
+ * request's k_rule must be GP_K_FIXED (1 <= k_fixed <= 126) or GP_K_PAPER
+ * (GP_EINVAL otherwise).  The vectors are stored in FP32 whatever
+ * cfg.storage says; no pass but the last reads or writes y.  Same arguments,
+ * outputs and blocking as gp_batch; infos report K and tail(K), with max_r_l1
+ * = 0 (not measured).
+ */
+gp_status gp_batch_clenshaw(gp_graph* g, int32_t count, const gp_request* reqs, gp_query_info* infos);
+
+/*
  * Autotuner for the batched form (the block width B; the paper has no
  * counterpart).  Times fused SpMM passes of the column engine on this graph at
  * each candidate width (powers of two in [8, 256]; widths == NULL means 32,

@@ -269,6 +269,14 @@ struct Store<__half> {
   }
 };
 
+// Update of a row from its neighbour sums acc = (P b)(u) and its own segment
+// p of the older vector (Q_{k-1}, or B_{k+2} in Clenshaw's form):
+//   forward:         r = 2 acc - d p, Q_{k+1} = r / d, y += c r, ||r||_1
+//   Clenshaw step:   b_k = 2 acc - d p (the source term is added after the
+//                    pass), B_k = b_k / d; no y
+//   Clenshaw final:  y = acc - d p (= P b_1 - b_2; c_0 e_s is added after)
+constexpr int kModeForward = 0, kModeClenshaw = 1, kModeClenshawFinal = 2;
+
 struct SpmmArgs {
   const int4* tiles;
   int64_t ntiles;
@@ -289,6 +297,7 @@ struct SpmmArgs {
   int ldb;              // row stride of the blocks, in elements
   int check;            // col_idx lists rows beyond the active ones (host: picks the kernel)
   int* tile_ctr;        // tiles claimed past the first two per warp (zeroed by the control kernel)
+  int mode;             // kModeForward, kModeClenshaw or kModeClenshawFinal
 };
 
 // Combine the entry groups' partial sums (lanes cg, cg + CG, cg + 2 CG, ...).
@@ -332,6 +341,7 @@ struct Lane {
   const unsigned char* zero;    // zero segment
   uint32_t rowG, rowP, rowN, rowY;  // row bytes of Q_k, Q_{k-1}, Q_{k+1}, y
   int na;
+  int mode;                     // kMode*: which row update the pass applies
   int cg, g, CG, EG, lane;
 };
 
@@ -394,14 +404,25 @@ __device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, co
   }
   const float inv = 1.0f / d;
   float out[PC];
+  if (L.mode == kModeClenshawFinal) {
+    // y = P b_1 - b_2 over the piece's columns (FP32 y, written, not read)
+#pragma unroll
+    for (int i = 0; i < PC; ++i) out[i] = acc[C0 + i] - d * prev[i];
+    unsigned char* yd = L.yseg + (uint64_t)(uint32_t)u * L.rowY + C0 * 4;
+#pragma unroll
+    for (int q = 0; q < PC / 4; ++q)
+      *reinterpret_cast<float4*>(yd + 16 * q) = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+    return;
+  }
+  const float two = 2.0f;
 #pragma unroll
   for (int i = 0; i < PC; ++i) {
     const int c = C0 + i;
     const ColState cs = L.s_col[c];
-    const float r = 2.0f * acc[c] - d * prev[i];
+    const float r = two * acc[c] - d * prev[i];
     out[i] = cs.active ? r * inv : prev[i];
     acc[c] = cs.active ? r : 0.f;
-    nrm[c] += fabsf(acc[c]);
+    if (L.mode == kModeForward) nrm[c] += fabsf(acc[c]);
   }
   unsigned char* dst = L.nseg + (uint64_t)(uint32_t)u * L.rowN + C0 * Store<TO>::bytes;
   if constexpr (PC % 8 == 0) {
@@ -469,7 +490,8 @@ __device__ __forceinline__ void own_round(const Lane& L, int64_t u, float d, int
 template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
-  constexpr int S = C::S, SB = C::SB, OP = C::OP, OWN = C::OWN;
+  constexpr int S = C::S, SB = C::SB, OP = C::OP;
+  const int OWN = L.mode == kModeForward ? C::OWN : OP;  // Clenshaw passes read no y
   const int d = t.b, nrows = t.a, EG = L.EG;
   const int nseq = (nrows + EG - 1) / EG;
   const int R = nseq * (d + OWN);
@@ -554,6 +576,16 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
   if (L.g == 0) {
     const float d = (float)a.ldeg[row];
     const float inv = 1.0f / d;
+    if (L.mode == kModeClenshawFinal) {  // y = P b_1 - b_2
+      float* yrow = a.y + row * a.ldb + L.cg * LC;
+#pragma unroll
+      for (int h = 0; h < LC / 8; ++h) {
+        const V8 pv = Store<TP>::load(a.qprev, row, a.ldb, L.cg * (LC / 8) + h);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) yrow[8 * h + i] = tot[8 * h + i] - d * pv.x[i];
+      }
+      return;
+    }
 #pragma unroll
     for (int h = 0; h < LC / 8; ++h) {
       const V8 pv = Store<TP>::load(a.qprev, row, a.ldb, L.cg * (LC / 8) + h);
@@ -565,10 +597,11 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
         const float r = 2.0f * tot[c] - d * pv.x[i];
         out.x[i] = cs.active ? r * inv : pv.x[i];
         tot[c] = cs.active ? r : 0.f;
-        nrm[c] += fabsf(tot[c]);
+        if (L.mode == kModeForward) nrm[c] += fabsf(tot[c]);
       }
       Store<TO>::store(a.qnext, row, a.ldb, L.cg * (LC / 8) + h, out);
     }
+    if (L.mode != kModeForward) return;  // Clenshaw steps: no y
     float4* yrow = reinterpret_cast<float4*>(a.y + row * a.ldb + L.cg * LC);
 #pragma unroll
     for (int q = 0; q < LC / 4; ++q) {
@@ -662,7 +695,8 @@ __device__ __forceinline__ void tile_chunk(const Lane& L, const BTile& t, const 
 template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
-  constexpr int S = C::S, SB = C::SB, OP = C::OP, OWN = C::OWN;
+  constexpr int S = C::S, SB = C::SB, OP = C::OP;
+  const int OWN = L.mode == kModeForward ? C::OWN : OP;  // Clenshaw passes read no y
   const int EG = L.EG, g = L.g;
   const int d = t.b;  // entries per row
   const int G = (d + EG - 1) / EG;
@@ -772,6 +806,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   L.rowN = (uint32_t)(a.ldb * Store<TO>::bytes);
   L.rowY = (uint32_t)(a.ldb * 4);
   L.na = (int)a.na;
+  L.mode = a.mode;
   float nrm[LC];
 #pragma unroll
   for (int i = 0; i < LC; ++i) nrm[i] = 0.f;
@@ -960,6 +995,17 @@ __global__ void output_columns_kernel(int64_t n, int64_t na, const int32_t* newi
       if (u < n) outs[t][u] = (OUT)s_tile[lane * B + cols[t]];
     __syncthreads();
   }
+}
+
+// Clenshaw's source term for every busy column j of the block:
+// buf[s_j][j] += c_k^(j) / d_{s_j} (a B vector: b_k += c_k e_s, stored as B = b / d),
+// or, with to_y, y[s_j][j] += c_0^(j).
+__global__ void clenshaw_inject_kernel(float* buf, int ldb, const ColState* col, const ColParam* par,
+                                       const int64_t* src, const float* inv_d, int B, int k, int to_y) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B || !col[j].active) return;
+  const float c = par[j].c[k];
+  buf[src[j] * ldb + j] += to_y ? c : c * inv_d[j];
 }
 
 int device_sms() {
@@ -1280,6 +1326,7 @@ void ColumnEngine::pass(int force_stage) {
   a.ldb = B_;
   a.check = g_.ci_beyond_active ? 1 : 0;
   a.tile_ctr = tile_ctr_;
+  a.mode = kModeForward;
   const bool prof = profile_;
   if (prof) {
     while (events_.size() < prof_marks_.size() * 2 + 2) {
@@ -1484,6 +1531,70 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
   }
 }
 
+void run_clenshaw(Graph& g, int count, const gp_request* reqs, gp_query_info* infos) {
+  for (int i = 0; i < count; ++i) {
+    const gp_request& r = reqs[i];
+    GP_REQUIRE(r.function == GP_FN_PPR || r.function == GP_FN_HKPR, "function must be GP_FN_PPR or GP_FN_HKPR");
+    GP_REQUIRE(r.source >= 0 && (int64_t)r.source < g.n, "source out of range");
+    if (r.function == GP_FN_PPR)
+      GP_REQUIRE(r.param > 0.0 && r.param < 1.0, "alpha must be in (0, 1)");
+    else
+      GP_REQUIRE(r.param > 0.0 && r.param <= 1e4, "t must be in (0, 1e4]");
+    GP_REQUIRE(r.l1_tol > 0.0 && r.l1_tol < 1.0, "l1_tol must be in (0, 1)");
+    GP_REQUIRE(r.out_dtype == GP_F64 || r.out_dtype == GP_F32, "out_dtype must be GP_F64 or GP_F32");
+    GP_REQUIRE(r.y_out != nullptr, "y_out is NULL");
+    GP_REQUIRE(r.k_rule == GP_K_FIXED || r.k_rule == GP_K_PAPER,
+               "Clenshaw's form needs K up front: k_rule must be GP_K_FIXED or GP_K_PAPER");
+    if (r.k_rule == GP_K_FIXED)
+      GP_REQUIRE(r.k_fixed >= 1 && r.k_fixed <= kMaxColK - 2, "k_fixed must be in [1, 126]");
+  }
+  if (count == 0) return;
+  int B = g.cfg.block_width;
+  if (B <= 0) B = std::min(256, std::max(8, (int)(1u << (32 - __builtin_clz((unsigned)std::max(count, 8) - 1)))));
+  BatchCache* bc = static_cast<BatchCache*>(g.batch);
+  if (!bc) {
+    bc = new BatchCache();
+    g.batch = bc;
+  }
+  if (!bc->eng || bc->B != B || bc->storage != g.cfg.storage) {
+    bc->eng.reset();
+    bc->eng.reset(new ColumnEngine(g, B, g.cfg.storage, g.stream));
+    bc->B = B;
+    bc->storage = g.cfg.storage;
+  }
+  ColumnEngine& eng = *bc->eng;
+  auto t0 = std::chrono::steady_clock::now();
+  for (int base = 0; base < count; base += B) {
+    const int nb = std::min(B, count - base);
+    std::vector<gp_request> block;
+    std::vector<uint64_t> tags;
+    for (int i = 0; i < nb; ++i) {
+      const gp_request& r = reqs[base + i];
+      if (g.h_deg[r.source] == 0) {
+        // P e_s = 0: y = f(0) e_s (the same answer as the forward form)
+        eng.restart();
+        eng.admit({r}, {(uint64_t)(base + i)});
+        if (infos) infos[base + i] = gp_query_info{0, 1, 0.0, 1.0, 0.0};
+        continue;
+      }
+      block.push_back(r);
+      tags.push_back((uint64_t)(base + i));
+    }
+    if (block.empty()) continue;
+    eng.restart();
+    for (const auto& f : eng.clenshaw(block, tags)) {
+      if (infos) {
+        gp_query_info& in = infos[f.tag];
+        in.K = f.K;
+        in.k16_from = f.k16_from;
+        in.tail_bound = f.tail_bound;
+        in.max_r_l1 = 0.0;  // not measured in the backward form
+        in.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ autotune
 
 namespace {
@@ -1652,6 +1763,120 @@ void ColumnEngine::flush_profile() {
     g_.prof_bytes += prof_marks_[i];
   }
   prof_marks_.clear();
+}
+
+// Clenshaw's backward form of the same truncated sum (Lemma 1), for up to B
+// queries with K fixed up front: b_{K+1} = b_{K+2} = 0,
+// b_k = c_k e_s + 2 P b_{k+1} - b_{k+2} for k = K .. 1, and
+// y = c_0 e_s + P b_1 - b_2.  Each step is one fused pass over the FP32 pair
+// (B_k = D^-1 b_k written over B_{k+2}); no pass touches y but the last, and
+// no norm or stop rule is needed.  Columns with K_j below the block's largest
+// K take c_k = 0 above K_j, so their b stay zero until step K_j.
+std::vector<ColumnEngine::Finished> ColumnEngine::clenshaw(const std::vector<gp_request>& reqs,
+                                                           const std::vector<uint64_t>& tags) {
+  const int nb = (int)reqs.size();
+  GP_REQUIRE(nb >= 1 && nb <= B_, "a Clenshaw block holds 1 .. B queries");
+  std::vector<ColState> cs(B_, ColState{0, 0.f});
+  std::vector<ColParam> par(B_);
+  std::vector<ColStat> st(B_, ColStat{0, 0, 0, 0.f});
+  std::vector<int64_t> src(B_, 0);
+  std::vector<float> invd(B_, 0.f);
+  int kmax = 1;
+  for (int j = 0; j < nb; ++j) {
+    const gp_request& r = reqs[j];
+    int K = r.k_rule == GP_K_FIXED ? r.k_fixed : paper_k(r.function, r.param, r.l1_tol);
+    K = std::max(1, std::min(K, kMaxColK - 2));
+    std::vector<double> c, tail;
+    cheb_coefficients(r.function, r.param, K, c, tail);
+    std::memset(&par[j], 0, sizeof(ColParam));
+    for (int k = 0; k <= K; ++k) par[j].c[k] = (float)c[k];
+    slots_[j].busy = true;
+    slots_[j].req = r;
+    slots_[j].tag = tags[j];
+    slots_[j].t_admit = std::chrono::steady_clock::now();
+    slots_[j].tails.assign(kMaxColK, 0.0);
+    slots_[j].tails[K] = tail[K];
+    cs[j] = ColState{1, 0.f};
+    st[j] = ColStat{K, K, 1, 0.f};
+    src[j] = g_.h_newid[r.source];
+    invd[j] = 1.0f / (float)g_.h_deg[r.source];
+    kmax = std::max(kmax, K);
+  }
+  int64_t* d_src = reinterpret_cast<int64_t*>(scratch_ + 4 * B_);
+  float* d_invd = reinterpret_cast<float*>(d_src + B_);
+  GP_CUDA_TRY(cudaMemcpyAsync(col_, cs.data(), sizeof(ColState) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(par_, par.data(), sizeof(ColParam) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(stat_, st.data(), sizeof(ColStat) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), sizeof(int64_t) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(d_invd, invd.data(), sizeof(float) * B_, cudaMemcpyHostToDevice, st_));
+  const size_t cells = (size_t)std::max<int64_t>(g_.n_active, 1) * B_;
+  GP_CUDA_TRY(cudaMemsetAsync(f_[0], 0, sizeof(float) * cells, st_));
+  GP_CUDA_TRY(cudaMemsetAsync(f_[1], 0, sizeof(float) * cells, st_));
+  GP_CUDA_TRY(cudaMemsetAsync(y_, 0, sizeof(float) * cells, st_));
+  int w = 8;
+  while (w < nb) w <<= 1;
+  bw_ = std::min(w, B_);
+  const int iblk = (B_ + 127) / 128;
+  auto inject = [&](float* buf, int k, int to_y) {
+    clenshaw_inject_kernel<<<iblk, 128, 0, st_>>>(buf, B_, col_, par_, d_src, d_invd, B_, k, to_y);
+    GP_LAUNCHED();
+  };
+  auto step = [&](int mode, float* cur, float* prv) {
+    GP_CUDA_TRY(cudaMemsetAsync(tile_ctr_, 0, sizeof(int), st_));
+    SpmmArgs a;
+    a.tiles = tiles_;
+    a.ntiles = ntiles_;
+    a.ci = g_.ci;
+    a.qcur = cur;
+    a.qprev = prv;
+    a.qnext = prv;
+    a.y = y_;
+    a.col = col_;
+    a.norm = norm_;
+    a.poff = poff_;
+    a.ldeg = ldeg_;
+    a.part = part_;
+    a.cnt = cnt_;
+    a.zero = zero_;
+    a.na = g_.n_active;
+    a.B = bw_;
+    a.ldb = B_;
+    a.check = g_.ci_beyond_active ? 1 : 0;
+    a.tile_ctr = tile_ctr_;
+    a.mode = mode;
+    launch_spmm<float, float, float>(a, st_);
+  };
+  int cur = 0, prv = 1;
+  inject(f_[cur], kmax, 0);  // b_K = c_K e_s
+  for (int k = kmax - 1; k >= 1; --k) {
+    step(kModeClenshaw, f_[cur], f_[prv]);  // b_k over b_{k+2}
+    inject(f_[prv], k, 0);
+    std::swap(cur, prv);
+  }
+  step(kModeClenshawFinal, f_[cur], f_[prv]);  // y = P b_1 - b_2
+  inject(y_, 0, 1);
+  passes_total_ += kmax;
+  std::vector<int> cols(nb);
+  for (int j = 0; j < nb; ++j) cols[j] = j;
+  write_outputs(cols);
+  std::vector<Finished> fin;
+  for (int j = 0; j < nb; ++j) {
+    Finished f;
+    f.slot = j;
+    f.tag = slots_[j].tag;
+    f.req = slots_[j].req;
+    f.K = st[j].K;
+    f.C = 0.f;
+    f.tail_bound = slots_[j].tails[f.K];
+    f.t_admit = slots_[j].t_admit;
+    f.k16_from = f.K + 1;
+    fin.push_back(f);
+    slots_[j].busy = false;
+  }
+  const std::vector<ColState> off(B_, ColState{0, 0.f});
+  GP_CUDA_TRY(cudaMemcpyAsync(col_, off.data(), sizeof(ColState) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaStreamSynchronize(st_));  // the host vectors are local
+  return fin;
 }
 
 void ColumnEngine::restart() {

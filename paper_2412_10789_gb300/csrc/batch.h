@@ -76,6 +76,10 @@ class ColumnEngine {
   // Move the busy columns into the first half of the pass width once at most
   // half of it is busy.  Returns whether the width was halved.
   bool compact();
+  // Clenshaw's backward form for a block of up to B requests with K fixed up
+  // front (engine restarted, no column busy); writes the outputs and returns
+  // the finished columns.
+  std::vector<Finished> clenshaw(const std::vector<gp_request>& reqs, const std::vector<uint64_t>& tags);
   // Time each SpMM pass with CUDA events (gp_batch under gp_profile_enable);
   // flush_profile() adds them to the graph's profile counters.
   void set_profile(bool on) { profile_ = on; }

@@ -146,6 +146,16 @@ extern "C" gp_status gp_poll(gp_graph* gh, uint64_t ticket, gp_query_info* info)
   return rc != GP_OK ? rc : st;
 }
 
+extern "C" gp_status gp_batch_clenshaw(gp_graph* gh, int32_t count, const gp_request* reqs, gp_query_info* infos) {
+  return guard([&] {
+    Graph* g = as_graph(gh);
+    GP_REQUIRE(count >= 0, "count must be >= 0");
+    GP_REQUIRE(count == 0 || reqs, "requests are NULL");
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    run_clenshaw(*g, count, reqs, infos);
+  });
+}
+
 extern "C" gp_status gp_autotune(gp_graph* gh, gp_dtype storage, const int32_t* widths, int32_t nwidths,
                                   int32_t* best_width, double* us_per_column_pass) {
   return guard([&] {

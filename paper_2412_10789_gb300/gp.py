@@ -119,6 +119,7 @@ def load_library():
             "gp_query": (ctypes.c_int, [vp, ctypes.POINTER(gp_request), pinfo]),
             "gp_power": (ctypes.c_int, [vp, i32, i32, dbl, dbl, ctypes.c_int, vp, ctypes.c_int, pinfo]),
             "gp_batch": (ctypes.c_int, [vp, i32, ctypes.POINTER(gp_request), pinfo]),
+            "gp_batch_clenshaw": (ctypes.c_int, [vp, i32, ctypes.POINTER(gp_request), pinfo]),
             "gp_submit": (ctypes.c_int, [vp, ctypes.POINTER(gp_request), ctypes.POINTER(u64)]),
             "gp_poll": (ctypes.c_int, [vp, u64, pinfo]),
             "gp_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
@@ -338,6 +339,14 @@ def gp_batch(g: Graph, requests, info=True):
     arr = (gp_request * len(requests))(*requests)
     infos = (gp_query_info * len(requests))() if info else None
     _check(_lib.gp_batch(g.handle, len(requests), arr, infos))
+    return [i.as_dict() for i in infos] if infos is not None else None
+
+
+def gp_batch_clenshaw(g: Graph, requests, info=True):
+    """The same packed columns in Clenshaw's backward form (K fixed up front)."""
+    arr = (gp_request * len(requests))(*requests)
+    infos = (gp_query_info * len(requests))() if info else None
+    _check(_lib.gp_batch_clenshaw(g.handle, len(requests), arr, infos))
     return [i.as_dict() for i in infos] if infos is not None else None
 
 

@@ -294,3 +294,36 @@ def test_batch_unvalidated_asymmetric_csr(gp):
             assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7, (i, e)
     finally:
         dg.close()
+
+
+@pytest.mark.parametrize("B", [8, 64])
+def test_clenshaw_matches_forward_sum(gp, B):
+    """Clenshaw's backward form evaluates the same truncated sum as Algorithm 3:
+    each column equals the oracle's forward ChebyPower at its K (FP32 batched
+    bar), for mixed functions, mixed K (1 and 2 included) and PAPER-rule K."""
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=B)
+    try:
+        srcs = list(gg.sources(g, 14, 43)) + [int(gg.top_degree_sources(g, 1)[0])]
+        ys = _outputs(g, len(srcs))
+        Ks = [1, 2] + [5 + 3 * (i % 8) for i in range(len(srcs) - 3)] + [0]
+        reqs = []
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            if Ks[i] == 0:
+                reqs.append(gp.make_request(fn, int(s), p, 1e-4, ys[i], k_rule=gp.GP_K_PAPER))
+            else:
+                reqs.append(gp.make_request(fn, int(s), p, 1e-6, ys[i], k_rule=gp.GP_K_FIXED, k_fixed=Ks[i]))
+        infos = gp.gp_batch_clenshaw(dg, reqs)
+        for i, s in enumerate(srcs):
+            fn, p = MIX[i % len(MIX)]
+            K = infos[i]["K"]
+            if Ks[i]:
+                assert K == Ks[i]
+            want = O.chebypower(g, int(s), KINDS[fn], p, K)
+            e = O.errors(g, want, ys[i].cpu().numpy())
+            assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7, (i, K, e)
+        with pytest.raises(Exception):
+            gp.gp_batch_clenshaw(dg, [gp.make_request(0, int(srcs[0]), 0.2, 1e-4, ys[0])])  # tail rule: no K up front
+    finally:
+        dg.close()
