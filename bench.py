@@ -125,6 +125,20 @@ def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32
                                   "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                                   "mean_launch_ms": ms, "launches": prof["step_launches"],
                                   "spmm_share_of_wall": prof["step_ms"] / 1000.0 / dt}}
+        if key == "fp32":
+            # Clenshaw's backward form of the same sums, each column at the K the forward form chose
+            kreqs = [gp.make_request(fn, s, p, tol, ys[i], k_rule=gp.GP_K_FIXED, k_fixed=max(1, infos[i]["K"]))
+                     for i, (fn, s, p) in enumerate(queries)]
+            gp.gp_batch_clenshaw(dg, kreqs)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                gp.gp_batch_clenshaw(dg, kreqs)
+            torch.cuda.synchronize()
+            dtc = dist_max(time.perf_counter() - t0, world, dev)
+            res["fp32_clenshaw_same_K"] = {"value": len(queries) * reps * world / dtc, "unit": UNIT,
+                                           "block_width": width, "queries": len(queries),
+                                           "K": "per column, the forward form's K at l1 <= 1e-6"}
         dg.close()
         del ys
     return res

@@ -1772,10 +1772,27 @@ void ColumnEngine::flush_profile() {
 // (B_k = D^-1 b_k written over B_{k+2}); no pass touches y but the last, and
 // no norm or stop rule is needed.  Columns with K_j below the block's largest
 // K take c_k = 0 above K_j, so their b stay zero until step K_j.
-std::vector<ColumnEngine::Finished> ColumnEngine::clenshaw(const std::vector<gp_request>& reqs,
-                                                           const std::vector<uint64_t>& tags) {
-  const int nb = (int)reqs.size();
+std::vector<ColumnEngine::Finished> ColumnEngine::clenshaw(const std::vector<gp_request>& reqs_in,
+                                                           const std::vector<uint64_t>& tags_in) {
+  const int nb = (int)reqs_in.size();
   GP_REQUIRE(nb >= 1 && nb <= B_, "a Clenshaw block holds 1 .. B queries");
+  // columns in descending K: at backward step k the started columns (K_j >= k)
+  // are a prefix, and the step's pass covers only that prefix
+  auto k_of = [&](const gp_request& r) {
+    const int K = r.k_rule == GP_K_FIXED ? r.k_fixed : paper_k(r.function, r.param, r.l1_tol);
+    return std::max(1, std::min(K, kMaxColK - 2));
+  };
+  std::vector<int> order(nb);
+  for (int j = 0; j < nb; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return k_of(reqs_in[x]) > k_of(reqs_in[y]); });
+  std::vector<gp_request> reqs(nb);
+  std::vector<uint64_t> tags(nb);
+  std::vector<int> kcol(nb);
+  for (int j = 0; j < nb; ++j) {
+    reqs[j] = reqs_in[order[j]];
+    tags[j] = tags_in[order[j]];
+    kcol[j] = k_of(reqs[j]);
+  }
   std::vector<ColState> cs(B_, ColState{0, 0.f});
   std::vector<ColParam> par(B_);
   std::vector<ColStat> st(B_, ColStat{0, 0, 0, 0.f});
@@ -1784,8 +1801,7 @@ std::vector<ColumnEngine::Finished> ColumnEngine::clenshaw(const std::vector<gp_
   int kmax = 1;
   for (int j = 0; j < nb; ++j) {
     const gp_request& r = reqs[j];
-    int K = r.k_rule == GP_K_FIXED ? r.k_fixed : paper_k(r.function, r.param, r.l1_tol);
-    K = std::max(1, std::min(K, kMaxColK - 2));
+    const int K = kcol[j];
     std::vector<double> c, tail;
     cheb_coefficients(r.function, r.param, K, c, tail);
     std::memset(&par[j], 0, sizeof(ColParam));
@@ -1813,9 +1829,13 @@ std::vector<ColumnEngine::Finished> ColumnEngine::clenshaw(const std::vector<gp_
   GP_CUDA_TRY(cudaMemsetAsync(f_[0], 0, sizeof(float) * cells, st_));
   GP_CUDA_TRY(cudaMemsetAsync(f_[1], 0, sizeof(float) * cells, st_));
   GP_CUDA_TRY(cudaMemsetAsync(y_, 0, sizeof(float) * cells, st_));
-  int w = 8;
-  while (w < nb) w <<= 1;
-  bw_ = std::min(w, B_);
+  auto width_for = [&](int k) {  // the prefix of columns with K_j >= k
+    int cnt = 0;
+    while (cnt < nb && kcol[cnt] >= k) ++cnt;
+    int w = 8;
+    while (w < cnt) w <<= 1;
+    return std::min(w, B_);
+  };
   const int iblk = (B_ + 127) / 128;
   auto inject = [&](float* buf, int k, int to_y) {
     clenshaw_inject_kernel<<<iblk, 128, 0, st_>>>(buf, B_, col_, par_, d_src, d_invd, B_, k, to_y);
@@ -1849,10 +1869,12 @@ std::vector<ColumnEngine::Finished> ColumnEngine::clenshaw(const std::vector<gp_
   int cur = 0, prv = 1;
   inject(f_[cur], kmax, 0);  // b_K = c_K e_s
   for (int k = kmax - 1; k >= 1; --k) {
+    bw_ = width_for(k + 1);  // columns with a nonzero b_{k+1}
     step(kModeClenshaw, f_[cur], f_[prv]);  // b_k over b_{k+2}
     inject(f_[prv], k, 0);
     std::swap(cur, prv);
   }
+  bw_ = width_for(1);
   step(kModeClenshawFinal, f_[cur], f_[prv]);  // y = P b_1 - b_2
   inject(y_, 0, 1);
   passes_total_ += kmax;
