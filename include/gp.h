@@ -196,6 +196,24 @@ gp_status gp_batch(gp_graph* g, int32_t count, const gp_request* reqs, gp_query_
 gp_status gp_batch_clenshaw(gp_graph* g, int32_t count, const gp_request* reqs, gp_query_info* infos);
 
 /*
+ * Generalized graph propagation of a feature matrix (Section "Generalizations",
+ * Def. general-gp and the theorem that follows it):
+ *     Z = f(D^-a A D^-b) X,  a + b = 1,  computed as  Z = D^-a f(P) D^a X,
+ * with f = SSPPR (param = alpha) or HKPR (param = t).  X and Z are n x F
+ * row-major FP32 arrays in the caller's node numbering, both in device memory
+ * (on_device = 1) or both in host memory (0; the library stages them).  The F
+ * features run as the columns of the batched engine (cfg.block_width or the
+ * next power of two up to 256 per block, cfg.storage for the vectors), each
+ * stopped by its own tail rule: ||D^a (z_f - z*_f)||_1 <= l1_tol ||D^a x_f||_1,
+ * which bounds ||z_f - z*_f||_1 by the same amount since every d_u^a >= 1 on
+ * the non-isolated nodes.  Nodes of degree 0 have a zero row and column in D^-a A D^-b
+ * (0^-a read as 0), so Z[u] = f(0) X[u] there.  a must be in [0, 1].  infos
+ * (nullable) receives F reports.
+ */
+gp_status gp_propagate(gp_graph* g, int32_t function, double param, double a, int32_t F, const float* X, float* Z,
+                       int on_device, double l1_tol, gp_query_info* infos);
+
+/*
  * Autotuner for the batched form (the block width B; the paper has no
  * counterpart).  Times fused SpMM passes of the column engine on this graph at
  * each candidate width (powers of two in [8, 256]; widths == NULL means 32,

@@ -275,7 +275,9 @@ struct Store<__half> {
 //   Clenshaw step:   b_k = 2 acc - d p (the source term is added after the
 //                    pass), B_k = b_k / d; no y
 //   Clenshaw final:  y = acc - d p (= P b_1 - b_2; c_0 e_s is added after)
-constexpr int kModeForward = 0, kModeClenshaw = 1, kModeClenshawFinal = 2;
+//   first step:      r_1 = acc (= P r_0), Q_1 = r_1 / d written to a fresh
+//                    buffer, y += c_1 r_1 (start vectors other than e_s)
+constexpr int kModeForward = 0, kModeClenshaw = 1, kModeClenshawFinal = 2, kModeFirst = 3;
 
 struct SpmmArgs {
   const int4* tiles;
@@ -414,15 +416,16 @@ __device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, co
       *reinterpret_cast<float4*>(yd + 16 * q) = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
     return;
   }
-  const float two = 2.0f;
+  const bool first = L.mode == kModeFirst;
+  const float two = first ? 1.0f : 2.0f, dp = first ? 0.0f : d;
 #pragma unroll
   for (int i = 0; i < PC; ++i) {
     const int c = C0 + i;
     const ColState cs = L.s_col[c];
-    const float r = two * acc[c] - d * prev[i];
+    const float r = two * acc[c] - dp * prev[i];
     out[i] = cs.active ? r * inv : prev[i];
     acc[c] = cs.active ? r : 0.f;
-    if (L.mode == kModeForward) nrm[c] += fabsf(acc[c]);
+    if (L.mode == kModeForward || first) nrm[c] += fabsf(acc[c]);
   }
   unsigned char* dst = L.nseg + (uint64_t)(uint32_t)u * L.rowN + C0 * Store<TO>::bytes;
   if constexpr (PC % 8 == 0) {
@@ -491,7 +494,7 @@ template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
   constexpr int S = C::S, SB = C::SB, OP = C::OP;
-  const int OWN = L.mode == kModeForward ? C::OWN : OP;  // Clenshaw passes read no y
+  const int OWN = L.mode == kModeForward || L.mode == kModeFirst ? C::OWN : OP;  // Clenshaw: no y
   const int d = t.b, nrows = t.a, EG = L.EG;
   const int nseq = (nrows + EG - 1) / EG;
   const int R = nseq * (d + OWN);
@@ -590,18 +593,19 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
     for (int h = 0; h < LC / 8; ++h) {
       const V8 pv = Store<TP>::load(a.qprev, row, a.ldb, L.cg * (LC / 8) + h);
       V8 out;
+      const bool first = L.mode == kModeFirst;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int c = 8 * h + i;
         const ColState cs = L.s_col[c];
-        const float r = 2.0f * tot[c] - d * pv.x[i];
+        const float r = first ? tot[c] : 2.0f * tot[c] - d * pv.x[i];
         out.x[i] = cs.active ? r * inv : pv.x[i];
         tot[c] = cs.active ? r : 0.f;
-        if (L.mode == kModeForward) nrm[c] += fabsf(tot[c]);
+        if (L.mode == kModeForward || first) nrm[c] += fabsf(tot[c]);
       }
       Store<TO>::store(a.qnext, row, a.ldb, L.cg * (LC / 8) + h, out);
     }
-    if (L.mode != kModeForward) return;  // Clenshaw steps: no y
+    if (L.mode == kModeClenshaw) return;  // Clenshaw steps: no y
     float4* yrow = reinterpret_cast<float4*>(a.y + row * a.ldb + L.cg * LC);
 #pragma unroll
     for (int q = 0; q < LC / 4; ++q) {
@@ -696,7 +700,7 @@ template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t, const int* ci_t, float nrm[LC]) {
   using C = Geo<TG, TP, TO, LC>;
   constexpr int S = C::S, SB = C::SB, OP = C::OP;
-  const int OWN = L.mode == kModeForward ? C::OWN : OP;  // Clenshaw passes read no y
+  const int OWN = L.mode == kModeForward || L.mode == kModeFirst ? C::OWN : OP;  // Clenshaw: no y
   const int EG = L.EG, g = L.g;
   const int d = t.b;  // entries per row
   const int G = (d + EG - 1) / EG;
@@ -1008,6 +1012,74 @@ __global__ void clenshaw_inject_kernel(float* buf, int ldb, const ColState* col,
   buf[src[j] * ldb + j] += to_y ? c : c * inv_d[j];
 }
 
+// ---- generalized propagation (gp_propagate): Z = f(D^-a A D^-b) X, a + b = 1,
+// computed as Z = D^-a f(P) D^a X (Section "Generalizations", the theorem on
+// generalized GP vectors), each feature a column of the block.
+
+// x'(u) = d_u^a X[u][f0 + j] over the active rows (relabelled order) into buf,
+// and the l1 norm of each column into colnorm.  A warp per row, lanes over
+// the columns (nb <= 256: at most 8 per lane).
+__global__ void prop_scale_kernel(int64_t na, int B, int nb, int F, int f0, const int32_t* order, const float* degf,
+                                  const float* X, float a, float* buf, float* colnorm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
+    const int64_t u = order[r];
+    const float sc = a == 0.f ? 1.f : powf(degf[r], a);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = lane + 32 * i;
+      if (j < nb) {
+        const float v = sc * X[u * F + f0 + j];
+        buf[r * B + j] = v;
+        part[i] += fabsf(v);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (lane + 32 * i < nb && part[i] != 0.f) atomicAdd(&colnorm[lane + 32 * i], part[i]);
+}
+
+// r_0 = x' / ||x'||_1 (so ||r_0||_1 = 1), Q_0 = r_0 / d over buf, y = c_0 r_0.
+__global__ void prop_init_kernel(int64_t na, int B, int nb, const float* degf, const float* colnorm, const float* c0,
+                                 float* buf, float* y) {
+  const int64_t total = na * (int64_t)nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / nb;
+    const int j = (int)(t - r * nb);
+    const float nrm = colnorm[j];
+    const float x = nrm > 0.f ? buf[r * B + j] / nrm : 0.f;
+    buf[r * B + j] = x / degf[r];
+    y[r * B + j] = c0[j] * x;
+  }
+}
+
+// Z[u][feat[t]] = d_u^-a ||x'||_1 y[newid[u]][cols[t]] for the active caller
+// rows u (isolated rows are written by prop_isolated_kernel).
+__global__ void prop_output_kernel(int64_t n, int64_t na, const int32_t* newid, const float* degf, float a,
+                                   const float* y, int B, const int* cols, const int* feat, int ncols,
+                                   const float* colnorm, int F, float* Z) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = newid[u];
+    if (i >= na) continue;
+    const float sc = a == 0.f ? 1.f : powf(degf[i], -a);
+    for (int t = 0; t < ncols; ++t) Z[u * F + feat[t]] = sc * colnorm[cols[t]] * y[i * B + cols[t]];
+  }
+}
+
+// Isolated nodes: D^-a A D^-b has a zero row and column there, so
+// Z[u][f] = f(0) X[u][f].
+__global__ void prop_isolated_kernel(int64_t n, int64_t na, const int32_t* newid, int F, float f0v, const float* X,
+                                     float* Z) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * (int64_t)F;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = t / F;
+    if (newid[u] >= na) Z[t] = f0v * X[t];
+  }
+}
+
 int device_sms() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1150,7 +1222,7 @@ void ColumnEngine::release() {
   Allocator& A = g_.alloc;
   for (void* p : {(void*)f_[0], (void*)f_[1], h_[0], h_[1], (void*)y_, (void*)col_, (void*)par_, (void*)stat_,
                   (void*)norm_, (void*)scratch_, outs_, stage_, (void*)tiles_, (void*)poff_, (void*)ldeg_,
-                  (void*)part_, (void*)cnt_, zero_, (void*)tile_ctr_})
+                  (void*)part_, (void*)cnt_, zero_, (void*)tile_ctr_, (void*)degf_})
     A.put(p);
   stat_ = nullptr;
   stage_ = nullptr;
@@ -1166,6 +1238,7 @@ void ColumnEngine::release() {
   ldeg_ = nullptr;
   zero_ = nullptr;
   tile_ctr_ = nullptr;
+  degf_ = nullptr;
   poff_ = nullptr;
   part_ = nullptr;
   cnt_ = nullptr;
@@ -1389,6 +1462,20 @@ std::vector<ColumnEngine::Finished> ColumnEngine::collect(bool force_all) {
 }
 
 void ColumnEngine::write_outputs(const std::vector<int>& cols) {
+  if (prop_.on) {
+    std::vector<int> feat(cols.size());
+    for (size_t t = 0; t < cols.size(); ++t) feat[t] = (int)slots_[cols[t]].tag;
+    int* d_cols = scratch_ + 2 * B_;
+    int* d_feat = scratch_;
+    GP_CUDA_TRY(cudaMemcpyAsync(d_cols, cols.data(), sizeof(int) * cols.size(), cudaMemcpyHostToDevice, st_));
+    GP_CUDA_TRY(cudaMemcpyAsync(d_feat, feat.data(), sizeof(int) * feat.size(), cudaMemcpyHostToDevice, st_));
+    prop_output_kernel<<<device_sms() * 8, 256, 0, st_>>>(g_.n, g_.n_active, g_.newid, prop_.degf, (float)prop_.a, y_,
+                                                          B_, d_cols, d_feat, (int)cols.size(), prop_.colnorm,
+                                                          prop_.F, prop_.Z);
+    GP_LAUNCHED();
+    GP_CUDA_TRY(cudaStreamSynchronize(st_));  // the host vectors are local
+    return;
+  }
   // one launch per output type and location; host outputs go through staging
   std::vector<int> dcol64, dcol32;
   std::vector<void*> p64, p32;
@@ -1592,6 +1679,78 @@ void run_clenshaw(Graph& g, int count, const gp_request* reqs, gp_query_info* in
         in.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       }
     }
+  }
+}
+
+void run_propagate(Graph& g, int function, double param, double a, int F, const float* X, float* Z, int on_device,
+                   double tol, gp_query_info* infos) {
+  GP_REQUIRE(function == GP_FN_PPR || function == GP_FN_HKPR, "function must be GP_FN_PPR or GP_FN_HKPR");
+  if (function == GP_FN_PPR)
+    GP_REQUIRE(param > 0.0 && param < 1.0, "alpha must be in (0, 1)");
+  else
+    GP_REQUIRE(param > 0.0 && param <= 1e4, "t must be in (0, 1e4]");
+  GP_REQUIRE(a >= 0.0 && a <= 1.0, "a must be in [0, 1] (b = 1 - a)");
+  GP_REQUIRE(F >= 1, "F must be >= 1");
+  GP_REQUIRE(X && Z, "X or Z is NULL");
+  GP_REQUIRE(tol > 0.0 && tol < 1.0, "l1_tol must be in (0, 1)");
+  const size_t bytes = sizeof(float) * (size_t)g.n * F;
+  Allocator& A = g.alloc;
+  float* dX = const_cast<float*>(X);
+  float* dZ = Z;
+  if (!on_device) {
+    dX = (float*)A.get(bytes);
+    dZ = (float*)A.get(bytes);
+  }
+  try {
+    cudaStream_t st = g.stream;
+    if (!on_device) GP_CUDA_TRY(cudaMemcpyAsync(dX, X, bytes, cudaMemcpyHostToDevice, st));
+    const double f0v = function == GP_FN_PPR ? param : std::exp(-param);
+    prop_isolated_kernel<<<device_sms() * 8, 256, 0, st>>>(g.n, g.n_active, g.newid, F, (float)f0v, dX, dZ);
+    GP_LAUNCHED();
+    if (g.n_active > 0) {
+      int B = g.cfg.block_width;
+      if (B <= 0) B = std::min(256, std::max(8, (int)(1u << (32 - __builtin_clz((unsigned)std::max(F, 8) - 1)))));
+      BatchCache* bc = static_cast<BatchCache*>(g.batch);
+      if (!bc) {
+        bc = new BatchCache();
+        g.batch = bc;
+      }
+      if (!bc->eng || bc->B != B || bc->storage != g.cfg.storage) {
+        bc->eng.reset();
+        bc->eng.reset(new ColumnEngine(g, B, g.cfg.storage, st));
+        bc->B = B;
+        bc->storage = g.cfg.storage;
+      }
+      auto t0 = std::chrono::steady_clock::now();
+      for (int f0 = 0; f0 < F; f0 += B) {
+        const int nb = std::min(B, F - f0);
+        for (const auto& f : bc->eng->propagate(dX, dZ, F, f0, nb, function, param, a, tol)) {
+          if (infos) {
+            gp_query_info& in = infos[f.tag];
+            in.K = f.K;
+            in.k16_from = f.k16_from;
+            in.tail_bound = f.tail_bound;
+            in.max_r_l1 = f.C;
+            in.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+          }
+        }
+      }
+    } else if (infos) {
+      for (int f = 0; f < F; ++f) infos[f] = gp_query_info{0, 1, 0.0, 1.0, 0.0};
+    }
+    if (!on_device) GP_CUDA_TRY(cudaMemcpyAsync(Z, dZ, bytes, cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaStreamSynchronize(g.stream);
+    if (!on_device) {
+      A.put(dX);
+      A.put(dZ);
+    }
+    throw;
+  }
+  if (!on_device) {
+    A.put(dX);
+    A.put(dZ);
   }
 }
 
@@ -1898,6 +2057,125 @@ std::vector<ColumnEngine::Finished> ColumnEngine::clenshaw(const std::vector<gp_
   const std::vector<ColState> off(B_, ColState{0, 0.f});
   GP_CUDA_TRY(cudaMemcpyAsync(col_, off.data(), sizeof(ColState) * B_, cudaMemcpyHostToDevice, st_));
   GP_CUDA_TRY(cudaStreamSynchronize(st_));  // the host vectors are local
+  return fin;
+}
+
+// One block of features f0 .. f0+nb-1 of a generalized propagation: start
+// columns r_0 = D^a x / ||D^a x||_1 (relabelled), a first pass r_1 = P r_0,
+// then forward passes with each column's own stop rule (relative to
+// ||D^a x||_1), compaction as columns retire, and Z written per retired
+// column.  X and Z are device arrays (n x F, row-major, caller order).
+std::vector<ColumnEngine::Finished> ColumnEngine::propagate(const float* X, float* Z, int F, int f0, int nb,
+                                                            int function, double param, double a, double tol) {
+  GP_REQUIRE(nb >= 1 && nb <= B_, "a propagation block holds 1 .. B features");
+  restart();
+  const int64_t na = std::max<int64_t>(g_.n_active, 1);
+  if (!degf_) {
+    degf_ = (float*)g_.alloc.get(sizeof(float) * na);
+    std::vector<float> d(na, 1.f);
+    for (int64_t i = 0; i < g_.n_active; ++i) d[i] = (float)(g_.h_rp_relabelled[i + 1] - g_.h_rp_relabelled[i]);
+    GP_CUDA_TRY(cudaMemcpyAsync(degf_, d.data(), sizeof(float) * na, cudaMemcpyHostToDevice, st_));
+    GP_CUDA_TRY(cudaStreamSynchronize(st_));
+  }
+  float* colnorm = reinterpret_cast<float*>(reinterpret_cast<int64_t*>(scratch_ + 4 * B_) + B_);  // B floats
+  float* c0dev = colnorm + B_;                                                                    // B floats
+  prop_ = Prop{true, Z, F, a, degf_, colnorm};
+  const size_t cells = (size_t)na * B_;
+  GP_CUDA_TRY(cudaMemsetAsync(f_[0], 0, sizeof(float) * cells, st_));
+  GP_CUDA_TRY(cudaMemsetAsync(f_[1], 0, sizeof(float) * cells, st_));
+  GP_CUDA_TRY(cudaMemsetAsync(y_, 0, sizeof(float) * cells, st_));
+  if (h_[0]) {
+    GP_CUDA_TRY(cudaMemsetAsync(h_[0], 0, 2 * cells, st_));
+    GP_CUDA_TRY(cudaMemsetAsync(h_[1], 0, 2 * cells, st_));
+  }
+  GP_CUDA_TRY(cudaMemsetAsync(colnorm, 0, sizeof(float) * B_, st_));
+  prop_scale_kernel<<<device_sms() * 8, 256, 0, st_>>>(g_.n_active, B_, nb, F, f0, g_.order, degf_, X, (float)a,
+                                                       f_[0], colnorm);
+  GP_LAUNCHED();
+  std::vector<double> c, tail;
+  cheb_coefficients(function, param, kcap_, c, tail);
+  ColParam p;
+  std::memset(&p, 0, sizeof(p));
+  for (int k = 0; k <= kcap_ && k < kMaxColK; ++k) {
+    p.c[k] = (float)c[k];
+    p.tail[k] = (float)tail[k];
+  }
+  p.tol = (float)tol;
+  p.kstop = 0;
+  p.warm = 0;
+  for (int k = 0; k <= kcap_ && k < kMaxColK; ++k)
+    if (tail[k] < g_.cfg.warmup_tail) {
+      p.warm = k;
+      break;
+    }
+  std::vector<ColState> cs(B_, ColState{0, 0.f});
+  std::vector<ColParam> par(B_, p);
+  std::vector<ColStat> st(B_, ColStat{0, 0, 0, 0.f});
+  std::vector<float> c0(B_, (float)c[0]);
+  for (int j = 0; j < nb; ++j) {
+    cs[j] = ColState{1, (float)c[1]};
+    st[j] = ColStat{1, 0, 0, 1.0f};  // ||r_0||_1 = 1 >= ||r_1||_1
+    slots_[j].busy = true;
+    std::memset(&slots_[j].req, 0, sizeof(gp_request));
+    slots_[j].req.function = function;
+    slots_[j].req.param = param;
+    slots_[j].req.l1_tol = tol;
+    slots_[j].tag = (uint64_t)(f0 + j);
+    slots_[j].t_admit = std::chrono::steady_clock::now();
+    slots_[j].tails.assign(tail.begin(), tail.end());
+    slots_[j].tails.resize(kMaxColK, 0.0);
+  }
+  GP_CUDA_TRY(cudaMemcpyAsync(col_, cs.data(), sizeof(ColState) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(par_, par.data(), sizeof(ColParam) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(stat_, st.data(), sizeof(ColStat) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemcpyAsync(c0dev, c0.data(), sizeof(float) * B_, cudaMemcpyHostToDevice, st_));
+  GP_CUDA_TRY(cudaMemsetAsync(norm_, 0, sizeof(float) * B_, st_));
+  prop_init_kernel<<<device_sms() * 8, 256, 0, st_>>>(g_.n_active, B_, nb, degf_, colnorm, c0dev, f_[0], y_);
+  GP_LAUNCHED();
+  active_ = nb;
+  warm_ = p.warm;
+  // first pass: r_1 = P r_0 into f_[1], y += c_1 r_1
+  {
+    int w = 8;
+    while (w < nb) w <<= 1;
+    bw_ = std::min(w, B_);
+    GP_CUDA_TRY(cudaMemsetAsync(tile_ctr_, 0, sizeof(int), st_));
+    SpmmArgs a1;
+    a1.tiles = tiles_;
+    a1.ntiles = ntiles_;
+    a1.ci = g_.ci;
+    a1.qcur = f_[0];
+    a1.qprev = f_[0];
+    a1.qnext = f_[1];
+    a1.y = y_;
+    a1.col = col_;
+    a1.norm = norm_;
+    a1.poff = poff_;
+    a1.ldeg = ldeg_;
+    a1.part = part_;
+    a1.cnt = cnt_;
+    a1.zero = zero_;
+    a1.na = g_.n_active;
+    a1.B = bw_;
+    a1.ldb = B_;
+    a1.check = g_.ci_beyond_active ? 1 : 0;
+    a1.tile_ctr = tile_ctr_;
+    a1.mode = kModeFirst;
+    launch_spmm<float, float, float>(a1, st_);
+  }
+  pass_ = 1;  // Q_1 in f_[1] (the buffer pass 1 gathers), Q_0 in f_[0]
+  std::vector<Finished> fin;
+  int since = 0;
+  while (active_ > 0) {
+    pass();
+    if (++since >= 4) {
+      since = 0;
+      for (auto& f : collect(false)) fin.push_back(f);
+      while (active_ > 0 && compact()) {
+      }
+    }
+  }
+  prop_.on = false;
   return fin;
 }
 

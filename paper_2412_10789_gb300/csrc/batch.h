@@ -80,6 +80,10 @@ class ColumnEngine {
   // front (engine restarted, no column busy); writes the outputs and returns
   // the finished columns.
   std::vector<Finished> clenshaw(const std::vector<gp_request>& reqs, const std::vector<uint64_t>& tags);
+  // Generalized propagation of features f0 .. f0+nb-1 of X (device, n x F,
+  // row-major) into Z: the finished columns (tag = feature index).
+  std::vector<Finished> propagate(const float* X, float* Z, int F, int f0, int nb, int function, double param,
+                                  double a, double tol);
   // Time each SpMM pass with CUDA events (gp_batch under gp_profile_enable);
   // flush_profile() adds them to the graph's profile counters.
   void set_profile(bool on) { profile_ = on; }
@@ -131,6 +135,15 @@ class ColumnEngine {
   int warm_ = 0;
   uint64_t passes_total_ = 0;
   bool profile_ = false;
+  struct Prop {  // output target while propagate() runs
+    bool on;
+    float* Z;
+    int F;
+    double a;
+    const float* degf;
+    const float* colnorm;
+  } prop_{false, nullptr, 0, 0.0, nullptr, nullptr};
+  float* degf_ = nullptr;  // degrees of the active rows (relabelled), for propagate()
   std::vector<cudaEvent_t> events_;
   std::vector<double> prof_marks_;  // algorithmic bytes of each timed pass
 };

@@ -156,6 +156,15 @@ extern "C" gp_status gp_batch_clenshaw(gp_graph* gh, int32_t count, const gp_req
   });
 }
 
+extern "C" gp_status gp_propagate(gp_graph* gh, int32_t function, double param, double a, int32_t F, const float* X,
+                                   float* Z, int on_device, double l1_tol, gp_query_info* infos) {
+  return guard([&] {
+    Graph* g = as_graph(gh);
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    run_propagate(*g, function, param, a, F, X, Z, on_device, l1_tol, infos);
+  });
+}
+
 extern "C" gp_status gp_autotune(gp_graph* gh, gp_dtype storage, const int32_t* widths, int32_t nwidths,
                                   int32_t* best_width, double* us_per_column_pass) {
   return guard([&] {

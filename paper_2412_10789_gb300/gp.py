@@ -120,6 +120,7 @@ def load_library():
             "gp_power": (ctypes.c_int, [vp, i32, i32, dbl, dbl, ctypes.c_int, vp, ctypes.c_int, pinfo]),
             "gp_batch": (ctypes.c_int, [vp, i32, ctypes.POINTER(gp_request), pinfo]),
             "gp_batch_clenshaw": (ctypes.c_int, [vp, i32, ctypes.POINTER(gp_request), pinfo]),
+            "gp_propagate": (ctypes.c_int, [vp, i32, dbl, dbl, i32, vp, vp, ctypes.c_int, dbl, pinfo]),
             "gp_submit": (ctypes.c_int, [vp, ctypes.POINTER(gp_request), ctypes.POINTER(u64)]),
             "gp_poll": (ctypes.c_int, [vp, u64, pinfo]),
             "gp_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
@@ -347,6 +348,21 @@ def gp_batch_clenshaw(g: Graph, requests, info=True):
     arr = (gp_request * len(requests))(*requests)
     infos = (gp_query_info * len(requests))() if info else None
     _check(_lib.gp_batch_clenshaw(g.handle, len(requests), arr, infos))
+    return [i.as_dict() for i in infos] if infos is not None else None
+
+
+def gp_propagate(g: Graph, function, param, a, X, Z, l1_tol, info=True):
+    """Z = f(D^-a A D^-b) X for an n x F row-major float32 X (numpy or torch, host or CUDA)."""
+    for m in (X, Z):
+        if str(m.dtype) not in ("float32", "torch.float32") or len(m.shape) != 2:
+            raise ValueError("X and Z must be n x F float32 arrays")
+    xp, xd = _ptr(X)
+    zp, zd = _ptr(Z)
+    if xd != zd:
+        raise ValueError("X and Z must both be on the host or both on the device")
+    F = int(X.shape[1])
+    infos = (gp_query_info * F)() if info else None
+    _check(_lib.gp_propagate(g.handle, int(function), float(param), float(a), F, xp, zp, xd, float(l1_tol), infos))
     return [i.as_dict() for i in infos] if infos is not None else None
 
 

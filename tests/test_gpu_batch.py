@@ -327,3 +327,57 @@ def test_clenshaw_matches_forward_sum(gp, B):
             gp.gp_batch_clenshaw(dg, [gp.make_request(0, int(srcs[0]), 0.2, 1e-4, ys[0])])  # tail rule: no K up front
     finally:
         dg.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_propagate_matches_definition(gp, storage):
+    """Z = f(D^-a A D^-b) X (a + b = 1) against the definition written out
+    with dense matrices: alpha (I - (1-alpha) M)^-1 X for SSPPR, expm(-t (I - M)) X
+    for HKPR, M = D^-a A D^-b with zero rows and columns at isolated nodes."""
+    import torch
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    g = gg.rmat(9, 8, seed=3)
+    n = g.n
+    assert (g.degree == 0).any()
+    A = np.zeros((n, n))
+    for u in range(n):
+        A[u, g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]]] = 1.0
+    d = g.degree.astype(np.float64)
+    rng = np.random.default_rng(7)
+    F = 12
+    X = rng.standard_normal((n, F)).astype(np.float32)
+    st = {"f32": gp.GP_F32, "bf16": gp.GP_BF16}[storage]
+    tol = 1e-6 if storage == "f32" else 1e-4
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=st, block_width=8)
+    try:
+        for fn, param in ((0, 0.2), (1, 4.0)):
+            for a in (0.0, 0.5, 1.0):
+                ds = np.where(d > 0, d, 1.0)
+                dma = np.where(d > 0, ds ** -a, 0.0)
+                dmb = np.where(d > 0, ds ** -(1.0 - a), 0.0)
+                M = dma[:, None] * A * dmb[None, :]
+                if fn == 0:
+                    want = param * np.linalg.solve(np.eye(n) - (1 - param) * M, X.astype(np.float64))
+                else:
+                    want = scipy_linalg.expm(-param * (np.eye(n) - M)) @ X.astype(np.float64)
+                Xd = torch.from_numpy(X).cuda()
+                Zd = torch.empty_like(Xd)
+                infos = gp.gp_propagate(dg, fn, param, a, Xd, Zd, tol)
+                Z = Zd.cpu().numpy().astype(np.float64)
+                for f in range(F):
+                    scale = np.abs(ds ** a * X[:, f]).sum()
+                    err = np.abs(Z[:, f] - want[:, f]).sum()
+                    assert err <= 2 * tol * scale, (fn, a, f, err, scale, infos[f])
+                iso = d == 0
+                f0 = param if fn == 0 else np.exp(-param)
+                assert np.allclose(Z[iso], f0 * X[iso].astype(np.float64), rtol=1e-6, atol=0)
+        # host arrays give the same result (column norms are summed by float
+        # atomics, so equal to rounding, not bit for bit)
+        Zh = np.zeros_like(X)
+        gp.gp_propagate(dg, 0, 0.2, 0.5, X, Zh, tol)
+        Xd = torch.from_numpy(X).cuda()
+        Zd = torch.empty_like(Xd)
+        gp.gp_propagate(dg, 0, 0.2, 0.5, Xd, Zd, tol)
+        assert np.allclose(Zh, Zd.cpu().numpy(), rtol=1e-4, atol=1e-6)
+    finally:
+        dg.close()
