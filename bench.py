@@ -61,7 +61,7 @@ def parse():
     p.add_argument("--batch-storage", default="bf16,fp32", help="storages of the batched form")
     p.add_argument("--batch-reps", type=int, default=3)
     p.add_argument("--workload", default="rmat22",
-                   choices=["rmat22", "rmat24_mixed", "chunglu24_serve", "rmat26_int64"],
+                   choices=["rmat22", "rmat24_mixed", "chunglu24_serve", "rmat26_int64", "rmat22_propagate"],
                    help="rmat22: the headline single-source workload; the others time the batched and "
                         "served forms on the larger graphs")
     p.add_argument("--requests", type=int, default=10000, help="chunglu24_serve: requests per load level")
@@ -568,6 +568,30 @@ def serve_poisson(gp, g, dev, args):
     return res
 
 
+def propagate_forms(gp, g, dev, reps):
+    """APPNP-style feature propagation: Z = f(D^-1/2 A D^-1/2) X, SSPPR alpha = 0.1,
+    for 128 seeded standard-normal features, BF16 and FP32 storage."""
+    import torch
+    gen = torch.Generator(device=dev).manual_seed(8)
+    X = torch.randn(g.n, 128, generator=gen, device=dev, dtype=torch.float32)
+    Z = torch.empty_like(X)
+    out = {}
+    for name, storage, tol in (("bf16_tol1e-4", gp.GP_BF16, 1e-4), ("fp32_tol1e-6", gp.GP_F32, 1e-6)):
+        dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=storage, block_width=128)
+        infos = gp.gp_propagate(dg, 0, 0.1, 0.5, X, Z, tol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            infos = gp.gp_propagate(dg, 0, 0.1, 0.5, X, Z, tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ks = [i["K"] for i in infos]
+        out[name] = {"value": 128 * reps / dt, "unit": "feature columns/s", "ms_per_call": 1000 * dt / reps,
+                     "K_min": min(ks), "K_max": max(ks), "features": 128, "alpha": 0.1, "a": 0.5}
+        dg.close()
+    return out
+
+
 def gg_sources(g, k, seed):
     import graphgen as gg
     return gg.sources(g, k, seed)
@@ -596,12 +620,19 @@ def run_workload(args, rank, world):
         queries = [(0, int(s), 0.2) for s in gg.sources(g, 64, 5)]
         forms = [("bf16_tol1e-4", gp.GP_BF16, 1e-4), ("fp32_tol1e-4", gp.GP_F32, 1e-4)]
         width, headline = 64, "bf16_tol1e-4"
+    elif args.workload == "rmat22_propagate":
+        g = gg.rmat(22, 16, 0.57, 0.19, 0.19, seed=2)
+        queries, forms, width, headline = None, None, 128, None
     else:
         g = gg.chung_lu(1 << 24, 30.0, 2.1, seed=4)
         queries, forms, width, headline = None, None, 256, None
     t_gen = time.perf_counter() - t_gen
     sampler.start()
-    if queries is not None:
+    if args.workload == "rmat22_propagate":
+        res = propagate_forms(gp, g, dev, args.batch_reps)
+        value, metric = res["bf16_tol1e-4"]["value"], "feature columns/s, Z = f(D^-a A D^-b) X (rmat22_propagate)"
+        queries = [None] * 128
+    elif queries is not None:
         res = batched_forms(gp, g, queries, forms, width, args.batch_reps, dev)
         value, metric = res[headline]["value"], f"batched queries/s at l1<={forms[0][2]:g} ({args.workload})"
     else:
@@ -610,7 +641,9 @@ def run_workload(args, rank, world):
     clocks = sampler.stop()
     if rank == 0:
         print(json.dumps({
-            "metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
+            "metric": metric, "value": value,
+            "unit": "feature columns/s" if args.workload == "rmat22_propagate" else UNIT, "n_gpus": world,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/bf16/f16 storage, f32 accumulate",
             "data": "synthetic",
             "config": {"workload": args.workload, "graph": g.name, "n": g.n, "nnz": g.nnz,
