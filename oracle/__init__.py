@@ -79,6 +79,8 @@ def _load():
         lib.or_chebypower_tol.argtypes = [i64, vp, vp, vp, vp, ci, dbl, vp, vp, vp]
         lib.or_chebypower_tol.restype = ci
         lib.or_cheb_basis.argtypes = [i64, vp, vp, vp, ci, vp]
+        lib.or_chebypush.argtypes = [i64, vp, vp, i64, vp, ci, vp, ci, vp, vp]
+        lib.or_chebypush.restype = ci
         lib.or_cheb_basis.restype = ci
         lib.or_errors.argtypes = [i64, vp, vp, vp, vp]
         lib.or_errors.restype = None
@@ -199,6 +201,33 @@ def chebypower_tol(g, s_or_x, kind, param: float, tol: float, Kmax: int = 200):
                                      c.ctypes.data, int(Kmax), float(tol), y.ctypes.data,
                                      ctypes.byref(K), nr.ctypes.data), "chebypower_tol")
     return y, int(K.value), nr[: K.value + 1].copy()
+
+
+def chebypush_eps(c: np.ndarray, K: int, eps_a: float) -> np.ndarray:
+    """The thresholds of Algorithm 4: eps_k = eps_a / (4 K sum_{l=k}^K |c_l|), k = 1..K-1 (index 0 unused)."""
+    eps = np.zeros(K + 1, dtype=np.float64)
+    for k in range(1, K):
+        eps[k] = eps_a / (4.0 * K * np.abs(c[k:K + 1]).sum())
+    return eps
+
+
+def chebypush(g, s: int, kind, param: float, K: int, eps_a: float | None = None, eps=None, coeffs=None,
+              rule: int = 0, return_r: bool = False):
+    """Algorithm 4 (ChebyPush) with truncation K: y = c_0 e_s + sum_{k=1}^{K-1} c_k r^_k|S_k.
+
+    Thresholds: eps_a (the algorithm's eps_k), or an explicit eps[0..K] array.
+    rule 0 pushes u when |r(u)| > eps_k d_u (the algorithm), rule 1 when
+    r(u)^2 >= eps_k d_u (the decisions of the paper's worked example)."""
+    c = cheb_coeffs(kind, param, K) if coeffs is None else np.ascontiguousarray(coeffs, np.float64)
+    if eps is None:
+        eps = chebypush_eps(c, K, eps_a)
+    eps = np.ascontiguousarray(eps, np.float64)
+    rp, ci = _csr(g)
+    y = np.empty(g.n, dtype=np.float64)
+    r = np.empty(g.n, dtype=np.float64)
+    _check(_load().or_chebypush(g.n, rp.ctypes.data, ci.ctypes.data, int(s), c.ctypes.data, int(K),
+                                eps.ctypes.data, int(rule), y.ctypes.data, r.ctypes.data), "chebypush")
+    return (y, r) if return_r else y
 
 
 def cheb_basis(g, s_or_x, K: int) -> np.ndarray:

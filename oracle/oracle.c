@@ -19,6 +19,7 @@
  *   or_chebypower      Algorithm 3 (ChebyPower), fixed truncation K, start vector x
  *   or_chebypower_tol  Algorithm 3 with K chosen by the l1 stopping reading
  *   or_cheb_basis      r_k = T_k(P) x for k = 0..K (Eq. res-recurrence), for pins
+ *   or_chebypush       Algorithm 4 (ChebyPush), the subset Chebyshev recurrence by pushes
  *   or_errors          the error measures of the error-metric definition, plus max-abs
  *
  * Threads: the only parallel loop is the row loop of or_P_apply; each row is
@@ -170,6 +171,58 @@ int or_chebypower(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, con
   }
   for (int64_t u = 0; u < n; ++u) y[u] += c[K] * rcur[u];
   free(rprev); free(rcur); free(pr);
+  return 0;
+}
+
+/* Algorithm 4 (ChebyPush): the subset Chebyshev recurrence (Def. of the
+ * subset recurrence, Eq. subset-cheby-implement) carried out by pushes:
+ *   y = c_0 e_s; r_cur = P e_s; r_new = -e_s; k = 1
+ *   while k < K:
+ *     for every u with |r_cur(u)| > eps[k] d_u          (rule 0: the algorithm)
+ *                  or r_cur(u)^2 >= eps[k] d_u         (rule 1: the decisions of
+ *                                                       the worked example)
+ *       y(u) += c_k r_cur(u)
+ *       r_new(v) += 2 r_cur(u) / d_u for every v in N(u)
+ *       r_cur(u) = -r_cur(u)
+ *     swap(r_cur, r_new); k += 1
+ * The pushes of one iteration write r_new only, so their order does not
+ * matter.  eps[1..K-1] are the per-iteration thresholds (the algorithm sets
+ * eps_k = eps_a / (4 K sum_{l=k}^K |c_l|)).  Writes y, and r_cur (= r^_K) to
+ * r_out when r_out is not NULL.  Returns 0, 1 for K < 1, 2 on allocation failure. */
+int or_chebypush(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t s, const double* c, int K,
+                 const double* eps, int rule, double* y, double* r_out) {
+  if (K < 1) return 1;
+  double* ra = (double*)calloc((size_t)n, sizeof(double));
+  double* rb = (double*)calloc((size_t)n, sizeof(double));
+  if (!ra || !rb) { free(ra); free(rb); return 2; }
+  double* rcur = ra;
+  double* rnew = rb;
+  for (int64_t u = 0; u < n; ++u) y[u] = 0.0;
+  y[s] = c[0];
+  {
+    double* es = (double*)calloc((size_t)n, sizeof(double));
+    if (!es) { free(ra); free(rb); return 2; }
+    es[s] = 1.0;
+    or_P_apply(n, row_ptr, col_idx, es, rcur);
+    free(es);
+  }
+  rnew[s] = -1.0;
+  for (int k = 1; k < K; ++k) {
+    for (int64_t u = 0; u < n; ++u) {
+      const double r = rcur[u], d = deg_of(row_ptr, u);
+      const int push = rule == 0 ? fabs(r) > eps[k] * d : r * r >= eps[k] * d;
+      if (!push) continue;
+      y[u] += c[k] * r;
+      for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) rnew[col_idx[e]] += 2.0 * r / d;
+      rcur[u] = -r;
+    }
+    double* t = rcur;
+    rcur = rnew;
+    rnew = t;
+  }
+  if (r_out) memcpy(r_out, rcur, sizeof(double) * (size_t)n);
+  free(ra);
+  free(rb);
   return 0;
 }
 

@@ -22,6 +22,12 @@ import oracle as O
 ORACLE_DIR = os.path.dirname(os.path.abspath(O.__file__))
 
 MUTANTS = {
+    # ChebyPush: the pushed node keeps r instead of -r (Eq. subset-cheby-implement)
+    "push_no_negation": ("      rcur[u] = -r;", "      rcur[u] = r;"),
+    # ChebyPush: r(u)/d_u pushed instead of 2 r(u)/d_u
+    "push_half": ("rnew[col_idx[e]] += 2.0 * r / d;", "rnew[col_idx[e]] += r / d;"),
+    # ChebyPush: the threshold against eps_k without the degree
+    "push_no_degree": ("fabs(r) > eps[k] * d", "fabs(r) > eps[k]"),
     # r_{k+1} = 2 P r_k + r_{k-1}
     "sign_of_rkm1": ("2.0 * pr[u] - r", "2.0 * pr[u] + r"),
     # D^-1 A instead of A D^-1 (divide by the row's degree)
@@ -29,8 +35,8 @@ MUTANTS = {
     # c_0 with 2/pi like the other coefficients
     "c0_weight": ("c[k] = (k == 0 ? 1.0 : 2.0) / OR_PI * integral;", "c[k] = 2.0 / OR_PI * integral;"),
     # the last term c_K r_K dropped
-    "drop_last_term": ("for (int64_t u = 0; u < n; ++u) y[u] += c[K] * rcur[u];\n  free(rprev); free(rcur); free(pr);\n  return 0;\n}\n\n/* Algorithm 3 with",
-                       "free(rprev); free(rcur); free(pr);\n  return 0;\n}\n\n/* Algorithm 3 with"),
+    "drop_last_term": ("for (int64_t u = 0; u < n; ++u) y[u] += c[K] * rcur[u];\n  free(rprev); free(rcur); free(pr);\n  return 0;\n}\n\n/* Algorithm 4 (ChebyPush)",
+                       "free(rprev); free(rcur); free(pr);\n  return 0;\n}\n\n/* Algorithm 4 (ChebyPush)"),
 }
 
 
@@ -72,6 +78,17 @@ def _pins_hold(M):
     want = np.array([np.sum(fl * np.cos(2 * np.pi * j * (u - 5) / n)) / n for u in range(n)])
     ok &= bool(np.max(np.abs(M.chebypower(cyc, 5, "ppr", 0.2, 80) - want)) < 1e-12)
     ok &= bool(np.max(np.abs(M.chebypower(g, s, "ppr", 0.2, 80) - M.dense_ppr(g, s, 0.2))) < 1e-12)
+    # ChebyPush: the worked example (Section 4) and Theorem 3's degree-normalised bound
+    c3e = np.array([0.0, 0.0, 0.0, 1.0])
+    _, r3 = M.chebypush(star, 1, "ppr", 0.2, 3, eps=np.full(4, 1 / 3), coeffs=c3e, rule=1, return_r=True)
+    ok &= np.allclose(r3, [5 / 3, 0, 0, 0], atol=1e-15)
+    _, r3b = M.chebypush(star, 1, "ppr", 0.2, 3, eps=np.full(4, 0.4), coeffs=c3e, rule=0, return_r=True)
+    ok &= np.allclose(r3b, [-1, 0, 0, 0], atol=1e-15)
+    gs = gg.erdos_renyi(200, 600, 3)
+    sh = int(np.argmax(gs.degree))
+    cc = M.cheb_coeffs("ppr", 0.2, 120)
+    yh = M.chebypush(gs, sh, "ppr", 0.2, 60, eps_a=1e-4, coeffs=cc[:61])
+    ok &= bool(np.max(np.abs(M.dense_ppr(gs, sh, 0.2) - yh) / np.maximum(gs.degree, 1)) < 1e-4)
     return bool(ok)
 
 

@@ -276,3 +276,62 @@ def test_thread_count_does_not_change_results():
     finally:
         O.set_threads(t0)
     assert np.array_equal(a, b)
+
+
+def test_chebypush_worked_example():
+    # Section 4 (ChebyPush), the illustrative example: the star v0 - {v1, v2, v3},
+    # f = T_3 from s = v1, threshold 1/3.  The pushes it describes (v0 at k = 1,
+    # v2 and v3 but not v1 at k = 2) are the decisions r^2 >= eps d (rule 1).
+    # After k = 1: r_cur = [0, -1/3, 2/3, 2/3]; after k = 2: r^_3 = [5/3, 0, 0, 0].
+    g = gg.from_edges(4, [(0, 1), (0, 2), (0, 3)], "star4")
+    c = np.array([0.0, 0.0, 0.0, 1.0])
+    eps = np.full(4, 1.0 / 3.0)
+    _, r2 = O.chebypush(g, 1, "ppr", 0.2, 2, eps=eps, coeffs=c[:3], rule=1, return_r=True)
+    assert np.allclose(r2, [0.0, -1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0], rtol=0, atol=1e-15)
+    y3, r3 = O.chebypush(g, 1, "ppr", 0.2, 3, eps=eps, coeffs=c, rule=1, return_r=True)
+    assert np.allclose(r3, [5.0 / 3.0, 0.0, 0.0, 0.0], rtol=0, atol=1e-15)
+    assert np.array_equal(y3, np.zeros(4))  # c_0 = c_1 = c_2 = 0
+    # the exact T_3(P) e_v1 is [1, 0, 0, 0]: the example's rounding of the recurrence
+    assert np.allclose(O.cheb_basis(g, 1, 3)[3], [1.0, 0.0, 0.0, 0.0], atol=1e-15)
+
+
+def test_chebypush_rule_of_the_algorithm_by_hand():
+    # Algorithm 4's own test |r(u)| > eps_k d_u on the same star, eps = 0.4, f = T_3:
+    # k = 1: r_cur = [1, 0, 0, 0]; the hub has |1| <= 0.4 * 3, so nothing is pushed
+    #        and the swap gives r_cur = [0, -1, 0, 0], r_new = [1, 0, 0, 0];
+    # k = 2: v1 has |-1| > 0.4 * 1: r_new(v0) += 2 * (-1) / 1 -> -1, r_cur(v1) -> 1;
+    # after the swap r^_3 = [-1, 0, 0, 0].
+    g = gg.from_edges(4, [(0, 1), (0, 2), (0, 3)], "star4")
+    _, r3 = O.chebypush(g, 1, "ppr", 0.2, 3, eps=np.full(4, 0.4), coeffs=np.array([0.0, 0.0, 0.0, 1.0]),
+                        rule=0, return_r=True)
+    assert np.array_equal(r3, np.array([-1.0, 0.0, 0.0, 0.0]))
+
+
+@pytest.mark.parametrize("kind,param", [("ppr", 0.2), ("hkpr", 5.0)])
+def test_chebypush_without_pruning_is_chebypower(kind, param):
+    # With every threshold 0, every node with r != 0 pushes: the subset recurrence
+    # is the full recurrence, y = sum_{k<K} c_k r_k and r^_K = T_K(P) e_s.
+    g = gg.erdos_renyi(300, 900, 5)
+    s = int(np.nonzero(g.degree)[0][0])
+    K = 18
+    c = O.cheb_coeffs(kind, param, K)
+    y, r = O.chebypush(g, s, kind, param, K, eps=np.zeros(K + 1), coeffs=c, rule=0, return_r=True)
+    assert np.max(np.abs(y - O.chebypower(g, s, kind, param, K - 1, coeffs=c[:K]))) < 1e-13
+    assert np.max(np.abs(r - O.cheb_basis(g, s, K)[K])) < 1e-12
+
+
+@pytest.mark.parametrize("gi", [0, 1])
+@pytest.mark.parametrize("kind,param", [("ppr", 0.2), ("hkpr", 5.0)])
+@pytest.mark.parametrize("eps_a", [1e-3, 1e-5])
+def test_chebypush_degree_normalised_bound(gi, kind, param, eps_a):
+    # Theorem 3: max_u |y(u) - y^(u)| / d_u < eps_a once K makes the truncation
+    # small (here tail(K-1) <= eps_a / 2: Algorithm 4 adds c_0 .. c_{K-1}).
+    g = [gg.erdos_renyi(400, 1600, 3), gg.chung_lu(500, 8.0, 2.1, seed=9)][gi]
+    s = int(np.argmax(g.degree))
+    c = O.cheb_coeffs(kind, param, 200)
+    tail = np.array([np.abs(c[k + 1:]).sum() for k in range(len(c))])
+    K = 1 + int(np.nonzero(tail <= eps_a / 2)[0][0])
+    yhat = O.chebypush(g, s, kind, param, K, eps_a=eps_a, coeffs=c[:K + 1])
+    ystar = O.dense_gp(g, s, kind, param)
+    d = np.maximum(g.degree, 1)
+    assert np.max(np.abs(ystar - yhat) / d) < eps_a
