@@ -214,6 +214,22 @@ gp_status gp_propagate(gp_graph* g, int32_t function, double param, double a, in
                        int on_device, double l1_tol, gp_query_info* infos);
 
 /*
+ * ChebyPush (Algorithm 4): the local form of the method.  The subset Chebyshev
+ * recurrence pushes, at iteration k, only the nodes u with
+ * |r^_k(u)| > eps_k d_u, eps_k = eps_a / (4 K sum_{l=k}^K |c_l|), and returns
+ * y^ = c_0 e_s + sum_{k=1}^{K-1} c_k r^_k restricted to the pushed nodes.
+ * Theorem 3 bounds the degree-normalised error: max_u |y(u) - y^(u)| / d_u <
+ * eps_a once the truncation is below eps_a / 2; K = 0 picks the smallest K
+ * with sum_{l>=K} |c_l| <= eps_a / 2 (1 <= K <= 1024 otherwise).  The vectors
+ * are FP64 on the device.  Output as in gp_ppr (out_dtype GP_F64 or GP_F32,
+ * device or host).  info (nullable): K; tail_bound = sum_{l>=K} |c_l|;
+ * max_r_l1 = the number of push items (frontier rows, long rows counted per
+ * 2048 entries) over all iterations.
+ */
+gp_status gp_chebypush(gp_graph* g, int32_t function, int32_t source, double param, double eps_a, int32_t K,
+                       gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info);
+
+/*
  * Autotuner for the batched form (the block width B; the paper has no
  * counterpart).  Times fused SpMM passes of the column engine on this graph at
  * each candidate width (powers of two in [8, 256]; widths == NULL means 32,

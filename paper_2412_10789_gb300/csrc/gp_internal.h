@@ -187,6 +187,9 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
 void run_clenshaw(Graph& g, int count, const gp_request* reqs, gp_query_info* infos);
 void run_propagate(Graph& g, int function, double param, double a, int F, const float* X, float* Z, int on_device,
                    double tol, gp_query_info* infos);
+// push.cu: ChebyPush (Algorithm 4) for one source.
+void run_chebypush(Graph& g, int function, int32_t source, double param, double eps_a, int K, gp_dtype out_dtype,
+                   void* y_out, int y_on_device, gp_query_info* info);
 // Block width with the least device time per column and pass on this graph
 // (cached per graph digest, storage and device unless widths are given).
 int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_per_column_pass);

@@ -1,0 +1,226 @@
+// ChebyPush (Algorithm 4) on the device: the subset Chebyshev recurrence of
+// Eq. (subset-cheby-implement), carried out by pushes from the nodes whose
+// residual exceeds the iteration's threshold.
+//
+//   y = c_0 e_s; r_cur = P e_s; r_new = -e_s
+//   for k = 1 .. K-1:
+//     S_k = {u : |r_cur(u)| > eps_k d_u},  eps_k = eps_a / (4 K sum_{l=k}^K |c_l|)
+//     for u in S_k: y(u) += c_k r_cur(u); r_new(v) += 2 r_cur(u) / d_u (v in N(u));
+//                   r_cur(u) = -r_cur(u)
+//     swap(r_cur, r_new)
+//
+// Each iteration is two kernels over the relabelled graph.  The scan reads
+// r_cur over all rows, applies the y update and the sign flip to the
+// nodes of S_k, and appends them to a frontier (a row longer than kPushChunk
+// entries becomes several frontier entries, so no warp is left with a hub).
+// The push scatters 2 r_cur(u) / d_u to the neighbours with FP64 atomic adds,
+// a warp per frontier entry.  The pushes of one iteration write r_new only, so
+// their order changes only the rounding of r_new; the vectors are FP64 so that
+// the threshold decisions follow the FP64 reference.  Scanning every row
+// costs 8 bytes per row and iteration; the pushes cost what the frontier
+// holds.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "gp_internal.h"
+
+namespace gp {
+
+namespace {
+
+constexpr int kPushChunk = 2048;  // entries of one frontier item
+
+template <typename RP>
+__global__ void push_init_kernel(const RP* rp, const int32_t* ci, int64_t s, double c0, double* rcur, double* rnew,
+                                 double* y) {
+  const int64_t beg = rp[s], end = rp[s + 1];
+  const double inv = 1.0 / (double)(end - beg);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    y[s] = c0;
+    rnew[s] = -1.0;
+  }
+  for (int64_t e = beg + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < end; e += (int64_t)gridDim.x * blockDim.x)
+    rcur[ci[e]] = inv;  // (P e_s)(v) = 1 / d_s for v in N(s)
+}
+
+// S_k: y += c_k r, r -> -r, and frontier items {u, chunk} with the pushed value.
+template <typename RP>
+__global__ void push_scan_kernel(int64_t n, const RP* rp, double* rcur, double* y, double ck, double eps,
+                                 int2* fr, double* fval, int* count) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; u0 < n;
+       u0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = u0 + lane;
+    int items = 0;  // a row of degree 0 (a node only an asymmetric CSR lists) pushes nothing
+    double r = 0.0, d = 0.0;
+    if (u < n) {
+      r = rcur[u];
+      d = (double)(rp[u + 1] - rp[u]);
+      if (fabs(r) > eps * d) {
+        y[u] += ck * r;
+        rcur[u] = -r;
+        items = (int)((rp[u + 1] - rp[u] + kPushChunk - 1) / kPushChunk);
+      }
+    }
+    // warp-aggregated reservation of the frontier slots
+    int incl = items;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(count, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    const int first = base + incl - items;
+    for (int j = 0; j < items; ++j) {
+      fr[first + j] = make_int2((int)u, j);
+      fval[first + j] = 2.0 * r / d;
+    }
+  }
+}
+
+template <typename RP>
+__global__ void push_scatter_kernel(const RP* rp, const int32_t* ci, const int2* fr, const double* fval,
+                                    const int* count, double* rnew) {
+  const int lane = threadIdx.x & 31;
+  const int n = *count;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const int2 it = fr[i];
+    const double v = fval[i];
+    const int64_t beg = rp[it.x] + (int64_t)it.y * kPushChunk;
+    const int64_t end = min(beg + (int64_t)kPushChunk, (int64_t)rp[it.x + 1]);
+    for (int64_t e = beg + lane; e < end; e += 32) atomicAdd(&rnew[ci[e]], v);
+  }
+}
+
+// y (relabelled) -> the caller's numbering.
+template <typename OUT>
+__global__ void push_output_kernel(int64_t n, const int32_t* newid, const double* y, OUT* out) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    out[u] = (OUT)y[newid[u]];
+}
+
+int sms() {
+  int dev = 0, s = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+  return s > 0 ? s : 1;
+}
+
+template <typename RP>
+void run_push_rp(Graph& g, int64_t s, const std::vector<double>& c, int K, double eps_a, double* rcur, double* rnew,
+                 double* y, int2* fr, double* fval, int* counts, int64_t* pushed) {
+  cudaStream_t st = g.stream;
+  const RP* rp = (const RP*)g.rp;
+  push_init_kernel<RP><<<4, 256, 0, st>>>(rp, g.ci, s, c[0], rcur, rnew, y);
+  GP_LAUNCHED();
+  const int grid = sms() * 8;
+  for (int k = 1; k < K; ++k) {
+    double tailK = 0.0;
+    for (int l = k; l <= K; ++l) tailK += std::fabs(c[l]);
+    const double eps = tailK > 0.0 ? eps_a / (4.0 * K * tailK) : 0.0;
+    push_scan_kernel<RP><<<grid, 256, 0, st>>>(g.n, rp, rcur, y, c[k], eps, fr, fval, counts + k);
+    GP_LAUNCHED();
+    push_scatter_kernel<RP><<<grid, 256, 0, st>>>(rp, g.ci, fr, fval, counts + k, rnew);
+    GP_LAUNCHED();
+    std::swap(rcur, rnew);
+  }
+  if (pushed) {
+    std::vector<int> h(K + 1, 0);
+    GP_CUDA_TRY(cudaMemcpyAsync(h.data(), counts, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaStreamSynchronize(st));
+    int64_t tot = 0;
+    for (int k = 1; k < K; ++k) tot += h[k];
+    *pushed = tot;
+  }
+}
+
+}  // namespace
+
+void run_chebypush(Graph& g, int function, int32_t source, double param, double eps_a, int K, gp_dtype out_dtype,
+                   void* y_out, int y_on_device, gp_query_info* info) {
+  GP_REQUIRE(function == GP_FN_PPR || function == GP_FN_HKPR, "function must be GP_FN_PPR or GP_FN_HKPR");
+  GP_REQUIRE(source >= 0 && (int64_t)source < g.n, "source out of range");
+  if (function == GP_FN_PPR)
+    GP_REQUIRE(param > 0.0 && param < 1.0, "alpha must be in (0, 1)");
+  else
+    GP_REQUIRE(param > 0.0 && param <= 1e4, "t must be in (0, 1e4]");
+  GP_REQUIRE(eps_a > 0.0 && eps_a < 1.0, "eps_a must be in (0, 1)");
+  GP_REQUIRE(K >= 0 && K <= 1024, "K must be in [0, 1024] (0: from eps_a)");
+  GP_REQUIRE(out_dtype == GP_F64 || out_dtype == GP_F32, "out_dtype must be GP_F64 or GP_F32");
+  GP_REQUIRE(y_out != nullptr, "y_out is NULL");
+  auto t0 = std::chrono::steady_clock::now();
+  // K: Algorithm 4 adds c_0 .. c_{K-1}; by default the smallest K whose
+  // truncation tail(K-1) = sum_{l>=K} |c_l| is at most eps_a / 2 (Theorem 3)
+  std::vector<double> c, tail;
+  cheb_coefficients(function, param, 1024, c, tail);
+  if (K == 0) {
+    K = 1;
+    while (K < 1024 && tail[K - 1] > eps_a / 2) ++K;
+  }
+  K = std::max(K, 1);
+  const size_t esz = out_dtype == GP_F64 ? 8 : 4;
+  cudaStream_t st = g.stream;
+  int64_t pushed = 0;
+  if (g.h_deg[source] == 0) {
+    // an isolated source: r_k = T_k(0) e_s; the sum is f(0) e_s up to the truncation
+    double v = 0.0;
+    for (int k = 0; k < K; k += 2) v += (k % 4 == 0 ? 1.0 : -1.0) * c[k];
+    std::vector<unsigned char> host(esz * g.n, 0);
+    if (out_dtype == GP_F64) reinterpret_cast<double*>(host.data())[source] = v;
+    else reinterpret_cast<float*>(host.data())[source] = (float)v;
+    GP_CUDA_TRY(cudaMemcpyAsync(y_out, host.data(), host.size(),
+                                y_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+    GP_CUDA_TRY(cudaStreamSynchronize(st));
+  } else {
+    Allocator& A = g.alloc;
+    const int64_t n = std::max<int64_t>(g.n, 1), na = std::max<int64_t>(g.n_active, 1);
+    double* ra = (double*)A.get(sizeof(double) * n);
+    double* rb = (double*)A.get(sizeof(double) * n);
+    double* y = (double*)A.get(sizeof(double) * n);
+    // frontier: at most one item per kPushChunk entries plus one per row
+    const int64_t cap = na + g.nnz / kPushChunk + 1;
+    int2* fr = (int2*)A.get(sizeof(int2) * cap);
+    double* fval = (double*)A.get(sizeof(double) * cap);
+    int* counts = (int*)A.get(sizeof(int) * (K + 1));
+    void* stage = y_on_device ? nullptr : A.get(esz * n);
+    try {
+      GP_CUDA_TRY(cudaMemsetAsync(ra, 0, sizeof(double) * n, st));
+      GP_CUDA_TRY(cudaMemsetAsync(rb, 0, sizeof(double) * n, st));
+      GP_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
+      GP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
+      const int64_t s = g.h_newid[source];
+      if (g.rp64)
+        run_push_rp<int64_t>(g, s, c, K, eps_a, ra, rb, y, fr, fval, counts, &pushed);
+      else
+        run_push_rp<int32_t>(g, s, c, K, eps_a, ra, rb, y, fr, fval, counts, &pushed);
+      void* dst = y_on_device ? y_out : stage;
+      const int grid = sms() * 4;
+      if (out_dtype == GP_F64)
+        push_output_kernel<double><<<grid, 256, 0, st>>>(g.n, g.newid, y, (double*)dst);
+      else
+        push_output_kernel<float><<<grid, 256, 0, st>>>(g.n, g.newid, y, (float*)dst);
+      GP_LAUNCHED();
+      if (!y_on_device) GP_CUDA_TRY(cudaMemcpyAsync(y_out, stage, esz * g.n, cudaMemcpyDeviceToHost, st));
+      GP_CUDA_TRY(cudaStreamSynchronize(st));
+    } catch (...) {
+      cudaStreamSynchronize(st);
+      for (void* p : {(void*)ra, (void*)rb, (void*)y, (void*)fr, (void*)fval, (void*)counts, stage}) A.put(p);
+      throw;
+    }
+    for (void* p : {(void*)ra, (void*)rb, (void*)y, (void*)fr, (void*)fval, (void*)counts, stage}) A.put(p);
+  }
+  if (info) {
+    info->K = K;
+    info->k16_from = K + 1;
+    info->tail_bound = tail[K - 1];
+    info->max_r_l1 = (double)pushed;  // for ChebyPush: frontier items pushed over all iterations
+    info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+}
+
+}  // namespace gp

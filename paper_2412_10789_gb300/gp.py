@@ -121,6 +121,7 @@ def load_library():
             "gp_batch": (ctypes.c_int, [vp, i32, ctypes.POINTER(gp_request), pinfo]),
             "gp_batch_clenshaw": (ctypes.c_int, [vp, i32, ctypes.POINTER(gp_request), pinfo]),
             "gp_propagate": (ctypes.c_int, [vp, i32, dbl, dbl, i32, vp, vp, ctypes.c_int, dbl, pinfo]),
+            "gp_chebypush": (ctypes.c_int, [vp, i32, i32, dbl, dbl, i32, ctypes.c_int, vp, ctypes.c_int, pinfo]),
             "gp_submit": (ctypes.c_int, [vp, ctypes.POINTER(gp_request), ctypes.POINTER(u64)]),
             "gp_poll": (ctypes.c_int, [vp, u64, pinfo]),
             "gp_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
@@ -364,6 +365,15 @@ def gp_propagate(g: Graph, function, param, a, X, Z, l1_tol, info=True):
     infos = (gp_query_info * F)() if info else None
     _check(_lib.gp_propagate(g.handle, int(function), float(param), float(a), F, xp, zp, xd, float(l1_tol), infos))
     return [i.as_dict() for i in infos] if infos is not None else None
+
+
+def gp_chebypush(g: Graph, function, source, param, eps_a, y_out, K=0, info=True):
+    """ChebyPush (Algorithm 4) from one source; K = 0 picks K from eps_a."""
+    ptr, on_dev = _ptr(y_out)
+    inf = gp_query_info() if info else None
+    _check(_lib.gp_chebypush(g.handle, int(function), int(source), float(param), float(eps_a), int(K),
+                             _out_dtype(y_out), ptr, on_dev, ctypes.byref(inf) if inf is not None else None))
+    return inf.as_dict() if inf is not None else None
 
 
 def gp_submit(g: Graph, request: gp_request) -> int:

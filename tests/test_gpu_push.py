@@ -1,0 +1,109 @@
+"""GPU tests of ChebyPush (Algorithm 4, gp_chebypush) against the FP64 oracle's
+Algorithm 4 (the algorithm's push rule |r(u)| > eps_k d_u) and against
+Theorem 3's degree-normalised bound, through the C ABI."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+KINDS = {0: "ppr", 1: "hkpr"}
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+    from paper_2412_10789_gb300 import build, gp as gpmod
+    build.build()
+    assert torch.cuda.is_available()
+    return gpmod
+
+
+_G = {}
+
+
+def graph(name):
+    if name not in _G:
+        _G[name] = {"er4096": lambda: gg.erdos_renyi(4096, 16384, 1), "rmat14": lambda: gg.rmat(14, 16, seed=2),
+                    "chunglu20k": lambda: gg.chung_lu(20011, 30.0, 2.1, seed=4)}[name]()
+    return _G[name]
+
+
+def _oracle_K(kind, param, eps_a):
+    c = O.cheb_coeffs(kind, param, 400)
+    tail = np.array([np.abs(c[k:]).sum() for k in range(1, len(c) + 1)])  # tail[k-1] = sum_{l>=k} |c_l|
+    K = 1
+    while tail[K - 1] > eps_a / 2:
+        K += 1
+    return K, c
+
+
+@pytest.mark.parametrize("gname", ["er4096", "rmat14", "chunglu20k"])
+@pytest.mark.parametrize("fn,param", [(0, 0.2), (1, 5.0)])
+@pytest.mark.parametrize("eps_a", [1e-3, 1e-6])
+def test_chebypush_matches_oracle(gp, gname, fn, param, eps_a):
+    import torch
+    g = graph(gname)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
+    try:
+        for s in list(gg.sources(g, 2, 29)) + [int(gg.top_degree_sources(g, 1)[0])]:
+            y = torch.empty(g.n, dtype=torch.float64, device="cuda")
+            info = gp.gp_chebypush(dg, fn, int(s), param, eps_a, y)
+            K, c = _oracle_K(KINDS[fn], param, eps_a)
+            assert info["K"] == K
+            want = O.chebypush(g, int(s), KINDS[fn], param, K, eps_a=eps_a, coeffs=c[:K + 1])
+            got = y.cpu().numpy()
+            assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, np.abs(want).max()), (s, np.max(np.abs(got - want)))
+    finally:
+        dg.close()
+
+
+@pytest.mark.parametrize("fn,param", [(0, 0.2), (1, 5.0)])
+def test_chebypush_degree_normalised_bound(gp, fn, param):
+    import torch
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
+    try:
+        d = np.maximum(g.degree, 1)
+        for eps_a in (1e-3, 1e-5):
+            for s in gg.sources(g, 3, 31):
+                y = torch.empty(g.n, dtype=torch.float64, device="cuda")
+                gp.gp_chebypush(dg, fn, int(s), param, eps_a, y)
+                ystar = O.chebypower(g, int(s), KINDS[fn], param, 150)
+                assert np.max(np.abs(ystar - y.cpu().numpy()) / d) < eps_a
+    finally:
+        dg.close()
+
+
+def test_chebypush_outputs_isolated_source_and_errors(gp):
+    import torch
+    g = gg.from_edges(40, [(i, i + 1) for i in range(30)] + [(35, 36)], "path_with_isolated")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
+    try:
+        # host FP64 and device FP32 outputs agree with the oracle
+        yh = np.zeros(g.n)
+        gp.gp_chebypush(dg, 0, 3, 0.2, 1e-6, yh)
+        K, c = _oracle_K("ppr", 0.2, 1e-6)
+        want = O.chebypush(g, 3, "ppr", 0.2, K, eps_a=1e-6, coeffs=c[:K + 1])
+        assert np.max(np.abs(yh - want)) < 1e-12
+        yf = torch.empty(g.n, dtype=torch.float32, device="cuda")
+        gp.gp_chebypush(dg, 0, 3, 0.2, 1e-6, yf)
+        assert np.max(np.abs(yf.cpu().numpy() - want)) < 1e-6
+        # node 33 is isolated: y = f(0) e_s up to the truncation, as the oracle's Algorithm 4
+        yi = np.zeros(g.n)
+        gp.gp_chebypush(dg, 1, 33, 4.0, 1e-8, yi)
+        K, c = _oracle_K("hkpr", 4.0, 1e-8)
+        want = O.chebypush(g, 33, "hkpr", 4.0, K, eps_a=1e-8, coeffs=c[:K + 1])
+        assert np.max(np.abs(yi - want)) < 1e-12
+        assert abs(yi[33] - np.exp(-4.0)) < 1e-8
+        # fixed K
+        info = gp.gp_chebypush(dg, 0, 3, 0.2, 1e-6, yh, K=7)
+        assert info["K"] == 7
+        for bad in (dict(source=-1), dict(source=40), dict(param=1.5), dict(eps=0.0), dict(K=-1)):
+            with pytest.raises(Exception):
+                gp.gp_chebypush(dg, 0, bad.get("source", 3), bad.get("param", 0.2), bad.get("eps", 1e-6), yh,
+                                K=bad.get("K", 0))
+    finally:
+        dg.close()
