@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--batch-storage", default="bf16,fp32", help="storages of the batched form")
     p.add_argument("--batch-reps", type=int, default=3)
     p.add_argument("--workload", default="rmat22",
-                   choices=["rmat22", "rmat24_mixed", "chunglu24_serve", "rmat26_int64", "rmat22_propagate"],
+                   choices=["rmat22", "rmat24_mixed", "chunglu24_serve", "rmat26_int64", "rmat22_propagate",
+                            "rmat22_push"],
                    help="rmat22: the headline single-source workload; the others time the batched and "
                         "served forms on the larger graphs")
     p.add_argument("--requests", type=int, default=10000, help="chunglu24_serve: requests per load level")
@@ -592,6 +593,31 @@ def propagate_forms(gp, g, dev, reps):
     return out
 
 
+def push_forms(gp, g, dev):
+    """ChebyPush (Algorithm 4) one query at a time on the headline queries
+    (64 sources x {SSPPR alpha=0.2, HKPR t=5}) at several eps_a (Theorem 3's
+    degree-normalised error), beside ChebyPower at l1 <= 1e-6."""
+    import torch
+    _, queries = workload(22, 64)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
+    y = torch.empty(g.n, dtype=torch.float64, device=dev)
+    out = {}
+    for name, eps in (("eps1e-3", 1e-3), ("eps1e-4", 1e-4), ("eps1e-5", 1e-5), ("eps1e-6", 1e-6)):
+        for fn, s, p in queries[:4]:
+            gp.gp_chebypush(dg, fn, s, p, eps, y)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        items = []
+        for fn, s, p in queries:
+            items.append(gp.gp_chebypush(dg, fn, s, p, eps, y)["max_r_l1"])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"value": len(queries) / dt, "unit": UNIT, "mean_push_items": float(np.mean(items)),
+                              "error": "max_u |y(u) - y^(u)| / d_u < eps_a (Theorem 3)"}
+    dg.close()
+    return out
+
+
 def gg_sources(g, k, seed):
     import graphgen as gg
     return gg.sources(g, k, seed)
@@ -620,7 +646,7 @@ def run_workload(args, rank, world):
         queries = [(0, int(s), 0.2) for s in gg.sources(g, 64, 5)]
         forms = [("bf16_tol1e-4", gp.GP_BF16, 1e-4), ("fp32_tol1e-4", gp.GP_F32, 1e-4)]
         width, headline = 64, "bf16_tol1e-4"
-    elif args.workload == "rmat22_propagate":
+    elif args.workload in ("rmat22_propagate", "rmat22_push"):
         g = gg.rmat(22, 16, 0.57, 0.19, 0.19, seed=2)
         queries, forms, width, headline = None, None, 128, None
     else:
@@ -628,7 +654,11 @@ def run_workload(args, rank, world):
         queries, forms, width, headline = None, None, 256, None
     t_gen = time.perf_counter() - t_gen
     sampler.start()
-    if args.workload == "rmat22_propagate":
+    if args.workload == "rmat22_push":
+        res = push_forms(gp, g, dev)
+        value, metric = res["eps1e-4"]["value"], "ChebyPush queries/s (rmat22_push)"
+        queries = [None] * 128
+    elif args.workload == "rmat22_propagate":
         res = propagate_forms(gp, g, dev, args.batch_reps)
         value, metric = res["bf16_tol1e-4"]["value"], "feature columns/s, Z = f(D^-a A D^-b) X (rmat22_propagate)"
         queries = [None] * 128
