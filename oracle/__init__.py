@@ -81,6 +81,12 @@ def _load():
         lib.or_cheb_basis.argtypes = [i64, vp, vp, vp, ci, vp]
         lib.or_chebypush.argtypes = [i64, vp, vp, i64, vp, ci, vp, ci, vp, vp]
         lib.or_chebypush.restype = ci
+        lib.or_bidirectional.argtypes = [i64, vp, vp, i64, dbl, vp, ci, dbl, dbl, ctypes.c_uint64, vp, vp]
+        lib.or_bidirectional.restype = ci
+        lib.or_walk_seed.argtypes = [ctypes.c_uint64, i64, i64]
+        lib.or_walk_seed.restype = ctypes.c_uint64
+        lib.or_alpha_walk.argtypes = [vp, vp, i64, dbl, ctypes.c_uint64]
+        lib.or_alpha_walk.restype = i64
         lib.or_cheb_basis.restype = ci
         lib.or_errors.argtypes = [i64, vp, vp, vp, vp]
         lib.or_errors.restype = None
@@ -228,6 +234,26 @@ def chebypush(g, s: int, kind, param: float, K: int, eps_a: float | None = None,
     _check(_load().or_chebypush(g.n, rp.ctypes.data, ci.ctypes.data, int(s), c.ctypes.data, int(K),
                                 eps.ctypes.data, int(rule), y.ctypes.data, r.ctypes.data), "chebypush")
     return (y, r) if return_r else y
+
+
+def bidirectional(g, s: int, alpha: float, K: int, eps_r: float, delta: float, seed: int, coeffs=None):
+    """Algorithm 5 (ChebyPush + alpha-random walks) for SSPPR; returns (pi^, number of walks)."""
+    c = cheb_coeffs("ppr", alpha, K) if coeffs is None else np.ascontiguousarray(coeffs, np.float64)
+    rp, ci = _csr(g)
+    y = np.empty(g.n, dtype=np.float64)
+    walks = ctypes.c_int64(0)
+    _check(_load().or_bidirectional(g.n, rp.ctypes.data, ci.ctypes.data, int(s), float(alpha), c.ctypes.data, int(K),
+                                    float(eps_r), float(delta), ctypes.c_uint64(seed), y.ctypes.data,
+                                    ctypes.byref(walks)), "bidirectional")
+    return y, int(walks.value)
+
+
+def alpha_walk(g, v: int, alpha: float, seed: int, j: int) -> int:
+    """The node where walk j from v stops (the generator of or_bidirectional)."""
+    rp, ci = _csr(g)
+    lib = _load()
+    return int(lib.or_alpha_walk(rp.ctypes.data, ci.ctypes.data, int(v), float(alpha),
+                                 lib.or_walk_seed(ctypes.c_uint64(seed), int(v), int(j))))
 
 
 def cheb_basis(g, s_or_x, K: int) -> np.ndarray:

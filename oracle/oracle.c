@@ -20,6 +20,7 @@
  *   or_chebypower_tol  Algorithm 3 with K chosen by the l1 stopping reading
  *   or_cheb_basis      r_k = T_k(P) x for k = 0..K (Eq. res-recurrence), for pins
  *   or_chebypush       Algorithm 4 (ChebyPush), the subset Chebyshev recurrence by pushes
+ *   or_bidirectional   Algorithm 5 (ChebyPush + alpha-random walks) for SSPPR
  *   or_errors          the error measures of the error-metric definition, plus max-abs
  *
  * Threads: the only parallel loop is the row loop of or_P_apply; each row is
@@ -223,6 +224,83 @@ int or_chebypush(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int6
   if (r_out) memcpy(r_out, rcur, sizeof(double) * (size_t)n);
   free(ra);
   free(rb);
+  return 0;
+}
+
+/* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", 2014): the state advances by the golden gamma and each output
+ * is the state mixed by its finaliser.  A random walk draws from its own
+ * stream, seeded from (seed, start node, walk index).                        */
+static uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static uint64_t sm64_next(uint64_t* state) {
+  *state += 0x9E3779B97F4A7C15ull;
+  return sm64_mix(*state);
+}
+uint64_t or_walk_seed(uint64_t seed, int64_t v, int64_t j) {
+  return sm64_mix(seed ^ sm64_mix((uint64_t)v * 0x9E3779B97F4A7C15ull + (uint64_t)j));
+}
+
+/* One alpha-random walk from v (Section "Generalizing to a Bidirectional
+ * Method"): at each step it stops with probability alpha, else it moves to a
+ * uniformly chosen neighbour.  Draws: u = (z >> 11) 2^-53 decides the stop
+ * (u < alpha); the neighbour is the ((z' >> 32) d >> 32)-th of the row.  A
+ * node without neighbours ends the walk.  Returns the node where it stops.    */
+int64_t or_alpha_walk(const int64_t* row_ptr, const int32_t* col_idx, int64_t v, double alpha, uint64_t state) {
+  for (;;) {
+    const uint64_t z = sm64_next(&state);
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    const int64_t d = row_ptr[v + 1] - row_ptr[v];
+    if (u < alpha || d == 0) return v;
+    const uint64_t z2 = sm64_next(&state);
+    v = col_idx[row_ptr[v] + (int64_t)(((z2 >> 32) * (uint64_t)d) >> 32)];
+  }
+}
+
+/* Algorithm 5 (ChebyPush + RW) for SSPPR with teleport alpha:
+ *   W = 2 (2 eps_r / 3 + 2) ln n / (eps_r^2 delta); r_max = sqrt(alpha) / W
+ *   pi^ = ChebyPush(G, f, s, K, r_max)                   (Algorithm 4, rule 0)
+ *   r = e_s - alpha^-1 [I - (1 - alpha) P] pi^
+ *   for every v with |r(v)| > 0: W_v = ceil(|r(v)| W) walks from v, walk j
+ *     drawing from the stream or_walk_seed(seed, v, j); pi^(u) += r(v) / W_v
+ *     at the node u where it stops
+ * c[0..K] are the SSPPR coefficients.  Writes pi^ to y, and (when not NULL)
+ * the total number of walks to *walks.  Returns 0, 1 for bad arguments, 2 on
+ * allocation failure.                                                         */
+int or_bidirectional(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t s, double alpha,
+                     const double* c, int K, double eps_r, double delta, uint64_t seed, double* y, int64_t* walks) {
+  if (K < 1 || n < 2 || !(alpha > 0.0 && alpha < 1.0)) return 1;
+  const double W = 2.0 * (2.0 * eps_r / 3.0 + 2.0) * log((double)n) / (eps_r * eps_r * delta);
+  const double rmax = sqrt(alpha) / W;
+  double* eps = (double*)malloc(sizeof(double) * (size_t)(K + 1));
+  double* r = (double*)malloc(sizeof(double) * (size_t)n);
+  double* pp = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!eps || !r || !pp) { free(eps); free(r); free(pp); return 2; }
+  eps[0] = 0.0;
+  for (int k = 1; k <= K; ++k) {
+    double t = 0.0;
+    for (int l = k; l <= K; ++l) t += fabs(c[l]);
+    eps[k] = t > 0.0 ? rmax / (4.0 * K * t) : 0.0;
+  }
+  int rc = or_chebypush(n, row_ptr, col_idx, s, c, K, eps, 0, y, NULL);
+  if (rc) { free(eps); free(r); free(pp); return rc; }
+  or_P_apply(n, row_ptr, col_idx, y, pp);
+  for (int64_t u = 0; u < n; ++u) r[u] = (u == s ? 1.0 : 0.0) - (y[u] - (1.0 - alpha) * pp[u]) / alpha;
+  int64_t total = 0;
+  for (int64_t v = 0; v < n; ++v) {
+    if (r[v] == 0.0) continue;
+    const int64_t Wv = (int64_t)ceil(fabs(r[v]) * W);
+    for (int64_t j = 0; j < Wv; ++j) {
+      const int64_t u = or_alpha_walk(row_ptr, col_idx, v, alpha, or_walk_seed(seed, v, j));
+      y[u] += r[v] / (double)Wv;
+    }
+    total += Wv;
+  }
+  if (walks) *walks = total;
+  free(eps); free(r); free(pp);
   return 0;
 }
 

@@ -22,6 +22,10 @@ import oracle as O
 ORACLE_DIR = os.path.dirname(os.path.abspath(O.__file__))
 
 MUTANTS = {
+    # alpha-walk: stops with probability 1 - alpha
+    "walk_stop_flipped": ("if (u < alpha || d == 0) return v;", "if (u >= alpha || d == 0) return v;"),
+    # Algorithm 5: the residual with the wrong sign of the (1 - alpha) P term
+    "residual_sign": ("(y[u] - (1.0 - alpha) * pp[u]) / alpha", "(y[u] + (1.0 - alpha) * pp[u]) / alpha"),
     # ChebyPush: the pushed node keeps r instead of -r (Eq. subset-cheby-implement)
     "push_no_negation": ("      rcur[u] = -r;", "      rcur[u] = r;"),
     # ChebyPush: r(u)/d_u pushed instead of 2 r(u)/d_u
@@ -89,6 +93,16 @@ def _pins_hold(M):
     cc = M.cheb_coeffs("ppr", 0.2, 120)
     yh = M.chebypush(gs, sh, "ppr", 0.2, 60, eps_a=1e-4, coeffs=cc[:61])
     ok &= bool(np.max(np.abs(M.dense_ppr(gs, sh, 0.2) - yh) / np.maximum(gs.degree, 1)) < 1e-4)
+    # alpha-walk endpoints follow PPR; Algorithm 5 is unbiased
+    rings = gg.from_edges(7, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (4, 5), (5, 6), (6, 4)])
+    ends = np.bincount([M.alpha_walk(rings, 1, 0.3, 11, j) for j in range(20000)], minlength=7) / 20000
+    want = M.dense_ppr(rings, 1, 0.3)
+    ok &= bool(np.all(np.abs(ends - want) <= 5 * np.sqrt(want * (1 - want) / 20000) + 1e-12))
+    ge = gg.erdos_renyi(120, 300, 7)
+    se = int(np.argmax(ge.degree))
+    runs = [M.bidirectional(ge, se, 0.2, 6, 1.0, 0.5, seed)[0] for seed in range(150)]
+    mean, sd = np.mean(runs, axis=0), np.std(runs, axis=0) / np.sqrt(150)
+    ok &= bool(np.all(np.abs(mean - M.dense_ppr(ge, se, 0.2)) <= 5 * sd + 1e-12))
     return bool(ok)
 
 

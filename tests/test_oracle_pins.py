@@ -335,3 +335,36 @@ def test_chebypush_degree_normalised_bound(gi, kind, param, eps_a):
     ystar = O.dense_gp(g, s, kind, param)
     d = np.maximum(g.degree, 1)
     assert np.max(np.abs(ystar - yhat) / d) < eps_a
+
+
+def test_alpha_walk_endpoints_follow_ppr():
+    # The node where an alpha-random walk from v stops is distributed as the SSPPR
+    # vector pi_v (each step stops with probability alpha, else moves to a uniform
+    # neighbour): the walk generator of Algorithm 5 against the dense solve.
+    g = gg.from_edges(7, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (4, 5), (5, 6), (6, 4)], "two_rings")
+    v, alpha, N = 1, 0.3, 40000
+    ends = np.bincount([O.alpha_walk(g, v, alpha, 11, j) for j in range(N)], minlength=g.n) / N
+    want = O.dense_ppr(g, v, alpha)
+    sd = np.sqrt(want * (1 - want) / N)
+    assert np.all(np.abs(ends - want) <= 5 * sd + 1e-12)
+
+
+def test_bidirectional_is_unbiased_and_meets_its_guarantee():
+    # Algorithm 5: E[pi^] = pi_s (each walk from v adds r(v)/W_v at its end, so the
+    # walks add r(v) pi_v in expectation, and pi_s = pi^_push + sum_v r(v) pi_v by
+    # the residual invariant).  A rough push (eps_r = 1, delta = 0.5) leaves a large
+    # residual; the mean over seeds converges to the dense solve.
+    g = gg.erdos_renyi(120, 300, 7)
+    s = int(np.argmax(g.degree))
+    alpha = 0.2
+    ystar = O.dense_ppr(g, s, alpha)
+    runs = [O.bidirectional(g, s, alpha, 6, 1.0, 0.5, seed)[0] for seed in range(300)]
+    mean = np.mean(runs, axis=0)
+    sd = np.std(runs, axis=0) / np.sqrt(len(runs))
+    assert np.std(runs, axis=0).max() > 1e-4  # the walks do change the estimate
+    assert np.all(np.abs(mean - ystar) <= 5 * sd + 1e-12)
+    # the (eps_r, delta) guarantee at eps_r = 0.5, delta = 0.01, one run
+    y, walks = O.bidirectional(g, s, alpha, 20, 0.5, 0.01, 3)
+    big = ystar > 0.01
+    assert np.all(np.abs(y[big] - ystar[big]) < 0.5 * ystar[big])
+    assert walks > 0
