@@ -230,6 +230,22 @@ gp_status gp_chebypush(gp_graph* g, int32_t function, int32_t source, double par
                        gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info);
 
 /*
+ * The bidirectional method for SSPPR (Algorithm 5, Section "Generalizing to a
+ * Bidirectional Method"): W = 2 (2 eps_r / 3 + 2) ln n / (eps_r^2 delta),
+ * r_max = sqrt(alpha) / W; pi^ = ChebyPush(G, f, s, K, r_max); the residual
+ * r = e_s - alpha^-1 [I - (1 - alpha) P] pi^; then ceil(|r(v)| W) alpha-random
+ * walks from every v with r(v) != 0, each adding r(v) / W_v where it stops.
+ * For nodes with pi(v) > delta the relative error is below eps_r with high
+ * probability.  Walk j from node v draws from a SplitMix64 stream seeded by
+ * (seed, v in the caller's numbering, j), so a seed fixes the result (up to
+ * the rounding order of the FP64 sums).  K = 0 takes the paper's
+ * K = ceil(alpha^-1/2 ln(1 / r_max)).  Output as in gp_ppr.  info (nullable):
+ * K; tail_bound = r_max; max_r_l1 = the number of walks.
+ */
+gp_status gp_ppr_bidirectional(gp_graph* g, int32_t source, double alpha, double eps_r, double delta, int32_t K,
+                               uint64_t seed, gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info);
+
+/*
  * Autotuner for the batched form (the block width B; the paper has no
  * counterpart).  Times fused SpMM passes of the column engine on this graph at
  * each candidate width (powers of two in [8, 256]; widths == NULL means 32,

@@ -174,6 +174,16 @@ extern "C" gp_status gp_chebypush(gp_graph* gh, int32_t function, int32_t source
   });
 }
 
+extern "C" gp_status gp_ppr_bidirectional(gp_graph* gh, int32_t source, double alpha, double eps_r, double delta,
+                                           int32_t K, uint64_t seed, gp_dtype out_dtype, void* y_out,
+                                           int y_on_device, gp_query_info* info) {
+  return guard([&] {
+    Graph* g = as_graph(gh);
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    run_bidirectional(*g, source, alpha, eps_r, delta, K, seed, out_dtype, y_out, y_on_device, info);
+  });
+}
+
 extern "C" gp_status gp_autotune(gp_graph* gh, gp_dtype storage, const int32_t* widths, int32_t nwidths,
                                   int32_t* best_width, double* us_per_column_pass) {
   return guard([&] {

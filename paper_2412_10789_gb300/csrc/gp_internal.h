@@ -190,6 +190,9 @@ void run_propagate(Graph& g, int function, double param, double a, int F, const 
 // push.cu: ChebyPush (Algorithm 4) for one source.
 void run_chebypush(Graph& g, int function, int32_t source, double param, double eps_a, int K, gp_dtype out_dtype,
                    void* y_out, int y_on_device, gp_query_info* info);
+// push.cu: Algorithm 5 (ChebyPush + alpha-random walks) for SSPPR.
+void run_bidirectional(Graph& g, int32_t source, double alpha, double eps_r, double delta, int K, uint64_t seed,
+                       gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info);
 // Block width with the least device time per column and pass on this graph
 // (cached per graph digest, storage and device unless widths are given).
 int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_per_column_pass);

@@ -104,6 +104,72 @@ __global__ void push_output_kernel(int64_t n, const int32_t* newid, const double
     out[u] = (OUT)y[newid[u]];
 }
 
+// ---- Algorithm 5 (ChebyPush + alpha-random walks) for SSPPR
+
+// SplitMix64 (Steele, Lea and Flood, 2014): state += golden gamma, output =
+// the finaliser of the state.  Walk j from node v (caller numbering) draws
+// from the stream seeded by mix(seed ^ mix(v * gamma + j)).
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t sm64_next(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  return sm64_mix(state);
+}
+
+// r = e_s - alpha^-1 [I - (1 - alpha) P] pi^ over all rows (FP64, a warp per row).
+template <typename RP>
+__global__ void bidir_residual_kernel(int64_t n, const RP* rp, const int32_t* ci, int64_t s, double alpha,
+                                      const double* y, double* r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    double acc = 0.0;
+    for (int64_t e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+      const int32_t v = ci[e];
+      const int64_t dv = rp[v + 1] - rp[v];
+      if (dv > 0) acc += y[v] / (double)dv;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) r[u] = (u == s ? 1.0 : 0.0) - (y[u] - (1.0 - alpha) * acc) / alpha;
+  }
+}
+
+// W_v = ceil(|r(v)| W) alpha-random walks from every v with r(v) != 0 (a warp
+// per v, its lanes over the walks); each adds r(v) / W_v where it stops.
+template <typename RP>
+__global__ void bidir_walk_kernel(int64_t n, const RP* rp, const int32_t* ci, const int32_t* order, double alpha,
+                                  double W, uint64_t seed, const double* r, double* y,
+                                  unsigned long long* walks) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long mine = 0;
+  for (int64_t v0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v0 < n; v0 += nw) {
+    const double rv = r[v0];
+    if (rv == 0.0) continue;
+    const int64_t Wv = (int64_t)ceil(fabs(rv) * W);
+    const double add = rv / (double)Wv;
+    const uint64_t vid = (uint64_t)order[v0];
+    for (int64_t j = lane; j < Wv; j += 32) {
+      uint64_t state = sm64_mix(seed ^ sm64_mix(vid * 0x9E3779B97F4A7C15ull + (uint64_t)j));
+      int64_t v = v0;
+      for (;;) {
+        const uint64_t z = sm64_next(state);
+        const double u01 = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        const int64_t d = rp[v + 1] - rp[v];
+        if (u01 < alpha || d == 0) break;
+        const uint64_t z2 = sm64_next(state);
+        v = ci[rp[v] + (int64_t)(((z2 >> 32) * (uint64_t)d) >> 32)];
+      }
+      atomicAdd(&y[v], add);
+    }
+    if (lane == 0) mine += (unsigned long long)Wv;
+  }
+  if (mine) atomicAdd(walks, mine);
+}
+
 int sms() {
   int dev = 0, s = 0;
   cudaGetDevice(&dev);
@@ -219,6 +285,86 @@ void run_chebypush(Graph& g, int function, int32_t source, double param, double 
     info->k16_from = K + 1;
     info->tail_bound = tail[K - 1];
     info->max_r_l1 = (double)pushed;  // for ChebyPush: frontier items pushed over all iterations
+    info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+}
+
+void run_bidirectional(Graph& g, int32_t source, double alpha, double eps_r, double delta, int K, uint64_t seed,
+                       gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info) {
+  GP_REQUIRE(source >= 0 && (int64_t)source < g.n, "source out of range");
+  GP_REQUIRE(alpha > 0.0 && alpha < 1.0, "alpha must be in (0, 1)");
+  GP_REQUIRE(eps_r > 0.0 && delta > 0.0 && delta <= 1.0, "eps_r must be > 0 and delta in (0, 1]");
+  GP_REQUIRE(g.n >= 2, "the graph needs at least two nodes");
+  GP_REQUIRE(K >= 0 && K <= 1024, "K must be in [0, 1024] (0: the paper's K)");
+  GP_REQUIRE(out_dtype == GP_F64 || out_dtype == GP_F32, "out_dtype must be GP_F64 or GP_F32");
+  GP_REQUIRE(y_out != nullptr, "y_out is NULL");
+  auto t0 = std::chrono::steady_clock::now();
+  const double W = 2.0 * (2.0 * eps_r / 3.0 + 2.0) * std::log((double)g.n) / (eps_r * eps_r * delta);
+  const double rmax = std::sqrt(alpha) / W;
+  if (K == 0) K = std::max(1, std::min(1024, (int)std::ceil(std::log(1.0 / rmax) / std::sqrt(alpha))));
+  std::vector<double> c, tail;
+  cheb_coefficients(GP_FN_PPR, alpha, std::max(K, 1), c, tail);
+  const size_t esz = out_dtype == GP_F64 ? 8 : 4;
+  cudaStream_t st = g.stream;
+  Allocator& A = g.alloc;
+  const int64_t n = g.n, na = std::max<int64_t>(g.n_active, 1);
+  double* ra = (double*)A.get(sizeof(double) * n);
+  double* rb = (double*)A.get(sizeof(double) * n);
+  double* y = (double*)A.get(sizeof(double) * n);
+  const int64_t cap = na + g.nnz / kPushChunk + 1;
+  int2* fr = (int2*)A.get(sizeof(int2) * cap);
+  double* fval = (double*)A.get(sizeof(double) * cap);
+  int* counts = (int*)A.get(sizeof(int) * (K + 1));
+  unsigned long long* walks = (unsigned long long*)A.get(sizeof(unsigned long long));
+  void* stage = y_on_device ? nullptr : A.get(esz * n);
+  unsigned long long h_walks = 0;
+  auto release = [&] {
+    for (void* p : {(void*)ra, (void*)rb, (void*)y, (void*)fr, (void*)fval, (void*)counts, (void*)walks, stage})
+      A.put(p);
+  };
+  try {
+    GP_CUDA_TRY(cudaMemsetAsync(ra, 0, sizeof(double) * n, st));
+    GP_CUDA_TRY(cudaMemsetAsync(rb, 0, sizeof(double) * n, st));
+    GP_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
+    GP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
+    GP_CUDA_TRY(cudaMemsetAsync(walks, 0, sizeof(unsigned long long), st));
+    const int64_t s = g.h_newid[source];
+    const int grid = sms() * 8;
+    // pi^ = ChebyPush(G, f, s, K, r_max); then r into ra (free after the push)
+    if (g.rp64) {
+      run_push_rp<int64_t>(g, s, c, K, rmax, ra, rb, y, fr, fval, counts, nullptr);
+      bidir_residual_kernel<int64_t><<<grid, 256, 0, st>>>(n, (const int64_t*)g.rp, g.ci, s, alpha, y, ra);
+      GP_LAUNCHED();
+      bidir_walk_kernel<int64_t><<<grid, 256, 0, st>>>(n, (const int64_t*)g.rp, g.ci, g.order, alpha, W, seed, ra,
+                                                       y, walks);
+    } else {
+      run_push_rp<int32_t>(g, s, c, K, rmax, ra, rb, y, fr, fval, counts, nullptr);
+      bidir_residual_kernel<int32_t><<<grid, 256, 0, st>>>(n, (const int32_t*)g.rp, g.ci, s, alpha, y, ra);
+      GP_LAUNCHED();
+      bidir_walk_kernel<int32_t><<<grid, 256, 0, st>>>(n, (const int32_t*)g.rp, g.ci, g.order, alpha, W, seed, ra,
+                                                       y, walks);
+    }
+    GP_LAUNCHED();
+    void* dst = y_on_device ? y_out : stage;
+    if (out_dtype == GP_F64)
+      push_output_kernel<double><<<sms() * 4, 256, 0, st>>>(g.n, g.newid, y, (double*)dst);
+    else
+      push_output_kernel<float><<<sms() * 4, 256, 0, st>>>(g.n, g.newid, y, (float*)dst);
+    GP_LAUNCHED();
+    if (!y_on_device) GP_CUDA_TRY(cudaMemcpyAsync(y_out, stage, esz * g.n, cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaMemcpyAsync(&h_walks, walks, sizeof(h_walks), cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    release();
+    throw;
+  }
+  release();
+  if (info) {
+    info->K = K;
+    info->k16_from = K + 1;
+    info->tail_bound = rmax;            // the push threshold r_max of Algorithm 5
+    info->max_r_l1 = (double)h_walks;   // random walks run
     info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
 }

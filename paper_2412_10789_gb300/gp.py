@@ -122,6 +122,8 @@ def load_library():
             "gp_batch_clenshaw": (ctypes.c_int, [vp, i32, ctypes.POINTER(gp_request), pinfo]),
             "gp_propagate": (ctypes.c_int, [vp, i32, dbl, dbl, i32, vp, vp, ctypes.c_int, dbl, pinfo]),
             "gp_chebypush": (ctypes.c_int, [vp, i32, i32, dbl, dbl, i32, ctypes.c_int, vp, ctypes.c_int, pinfo]),
+            "gp_ppr_bidirectional": (ctypes.c_int, [vp, i32, dbl, dbl, dbl, i32, u64, ctypes.c_int, vp,
+                                                    ctypes.c_int, pinfo]),
             "gp_submit": (ctypes.c_int, [vp, ctypes.POINTER(gp_request), ctypes.POINTER(u64)]),
             "gp_poll": (ctypes.c_int, [vp, u64, pinfo]),
             "gp_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
@@ -373,6 +375,16 @@ def gp_chebypush(g: Graph, function, source, param, eps_a, y_out, K=0, info=True
     inf = gp_query_info() if info else None
     _check(_lib.gp_chebypush(g.handle, int(function), int(source), float(param), float(eps_a), int(K),
                              _out_dtype(y_out), ptr, on_dev, ctypes.byref(inf) if inf is not None else None))
+    return inf.as_dict() if inf is not None else None
+
+
+def gp_ppr_bidirectional(g: Graph, source, alpha, eps_r, delta, y_out, K=0, seed=0, info=True):
+    """Algorithm 5 (ChebyPush + alpha-random walks) for SSPPR."""
+    ptr, on_dev = _ptr(y_out)
+    inf = gp_query_info() if info else None
+    _check(_lib.gp_ppr_bidirectional(g.handle, int(source), float(alpha), float(eps_r), float(delta), int(K),
+                                     int(seed), _out_dtype(y_out), ptr, on_dev,
+                                     ctypes.byref(inf) if inf is not None else None))
     return inf.as_dict() if inf is not None else None
 
 

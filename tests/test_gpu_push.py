@@ -107,3 +107,54 @@ def test_chebypush_outputs_isolated_source_and_errors(gp):
                                 K=bad.get("K", 0))
     finally:
         dg.close()
+
+
+def _paper_K(alpha, eps_r, delta, n):
+    W = 2 * (2 * eps_r / 3 + 2) * np.log(n) / (eps_r ** 2 * delta)
+    return max(1, int(np.ceil(np.log(W / np.sqrt(alpha)) / np.sqrt(alpha))))
+
+
+@pytest.mark.parametrize("gname", ["er4096", "rmat14"])
+@pytest.mark.parametrize("eps_r,delta", [(1.0, 0.5), (0.5, 1e-3)])
+def test_bidirectional_matches_oracle(gp, gname, eps_r, delta):
+    """Same generator streams, same walks: the device equals the oracle's
+    Algorithm 5 up to the rounding order of its FP64 sums."""
+    import torch
+    g = graph(gname)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
+    try:
+        alpha = 0.2
+        K = _paper_K(alpha, eps_r, delta, g.n)
+        for s, seed in zip(list(gg.sources(g, 2, 37)) + [int(gg.top_degree_sources(g, 1)[0])], (1, 2, 3)):
+            y = torch.empty(g.n, dtype=torch.float64, device="cuda")
+            info = gp.gp_ppr_bidirectional(dg, int(s), alpha, eps_r, delta, y, seed=seed)
+            assert info["K"] == K
+            want, walks = O.bidirectional(g, int(s), alpha, K, eps_r, delta, seed)
+            assert int(info["max_r_l1"]) == walks
+            got = y.cpu().numpy()
+            assert np.max(np.abs(got - want)) <= 1e-12, (s, np.max(np.abs(got - want)))
+        # another seed draws other walks
+        y2 = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        gp.gp_ppr_bidirectional(dg, int(s), alpha, eps_r, delta, y2, seed=99)
+        if eps_r == 1.0:
+            assert not torch.equal(y, y2)
+    finally:
+        dg.close()
+
+
+def test_bidirectional_isolated_source_and_errors(gp):
+    g = gg.from_edges(40, [(i, i + 1) for i in range(30)] + [(35, 36)], "path_with_isolated")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
+    try:
+        y = np.zeros(g.n)
+        K = _paper_K(0.2, 0.5, 0.01, g.n)
+        gp.gp_ppr_bidirectional(dg, 33, 0.2, 0.5, 0.01, y, seed=4)
+        want, _ = O.bidirectional(g, 33, 0.2, K, 0.5, 0.01, 4)
+        assert np.max(np.abs(y - want)) < 1e-12
+        assert abs(y[33] - 0.2) < 1e-6
+        for bad in (dict(source=40), dict(alpha=1.0), dict(eps_r=0.0), dict(delta=2.0)):
+            with pytest.raises(Exception):
+                gp.gp_ppr_bidirectional(dg, bad.get("source", 3), bad.get("alpha", 0.2), bad.get("eps_r", 0.5),
+                                        bad.get("delta", 0.01), y)
+    finally:
+        dg.close()
