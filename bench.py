@@ -614,6 +614,19 @@ def push_forms(gp, g, dev):
         dt = time.perf_counter() - t0
         out[name] = {"value": len(queries) / dt, "unit": UNIT, "mean_push_items": float(np.mean(items)),
                               "error": "max_u |y(u) - y^(u)| / d_u < eps_a (Theorem 3)"}
+    # Algorithm 5 for the SSPPR queries (eps_r = 0.5; delta = 1e-4 and 1 / n)
+    ppr = [q for q in queries if q[0] == 0]
+    for name, delta in (("bidirectional_delta1e-4", 1e-4), ("bidirectional_delta1/n", 1.0 / g.n)):
+        gp.gp_ppr_bidirectional(dg, ppr[0][1], 0.2, 0.5, delta, y, seed=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        walks = []
+        for i, (_, s, p) in enumerate(ppr):
+            walks.append(gp.gp_ppr_bidirectional(dg, s, p, 0.5, delta, y, seed=i)["max_r_l1"])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"value": len(ppr) / dt, "unit": UNIT, "mean_walks": float(np.mean(walks)),
+                     "error": "relative error < 0.5 where pi(v) > delta, w.h.p. (Algorithm 5)"}
     dg.close()
     return out
 
