@@ -158,3 +158,28 @@ def test_bidirectional_isolated_source_and_errors(gp):
                                         bad.get("delta", 0.01), y)
     finally:
         dg.close()
+
+
+def test_int64_row_offsets(gp):
+    """The same queries with row offsets stored as int64 (cfg.row_ptr_64): the
+    ChebyPush, bidirectional, batched and propagation paths agree with the oracle."""
+    import torch
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, row_ptr_64=1, block_width=16)
+    try:
+        s = int(gg.sources(g, 1, 41)[0])
+        y = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        gp.gp_chebypush(dg, 0, s, 0.2, 1e-5, y, K=20)
+        assert np.max(np.abs(y.cpu().numpy() - O.chebypush(g, s, "ppr", 0.2, 20, eps_a=1e-5))) < 1e-12
+        K = _paper_K(0.2, 1.0, 0.5, g.n)
+        gp.gp_ppr_bidirectional(dg, s, 0.2, 1.0, 0.5, y, seed=5)
+        assert np.max(np.abs(y.cpu().numpy() - O.bidirectional(g, s, 0.2, K, 1.0, 0.5, 5)[0])) < 1e-12
+        ys = [torch.empty(g.n, dtype=torch.float64, device="cuda") for _ in range(3)]
+        reqs = [gp.make_request(1, int(v), 5.0, 1e-6, ys[i], k_rule=gp.GP_K_FIXED, k_fixed=15)
+                for i, v in enumerate(gg.sources(g, 3, 43))]
+        gp.gp_batch(dg, reqs)
+        for i, v in enumerate(gg.sources(g, 3, 43)):
+            e = O.errors(g, O.chebypower(g, int(v), "hkpr", 5.0, 15), ys[i].cpu().numpy())
+            assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7, e
+    finally:
+        dg.close()
