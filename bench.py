@@ -455,7 +455,7 @@ def run_ours(args, rank, world):
     bytes_per_launch = prof["step_bytes"] / max(prof["step_launches"], 1)
     achieved = bytes_per_launch / (mean_launch_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(), "peak_kind": peak_kind, "kernel": "cheb_step_kernel",
+                "traffic": ncu_traffic(), "peak_kind": peak_kind, "kernel": "cheb_step_kernel (+ cheb_long_kernel, one pass)",
                 "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_launch_ms,
                 "launches": prof["step_launches"]}
     if rank == 0:

@@ -191,6 +191,11 @@ void launch_step(Graph& g, StepArgs& a, int grid) {
   }
   cheb_step_kernel<RP><<<grid, kStepThreads, g.sched.smem_bytes, g.stream>>>(a);
   GP_LAUNCHED();
+  if (a.nlong > 0) {
+    const int lgrid = (int)std::min<int64_t>((a.nlong + kLongWarps - 1) / kLongWarps, (int64_t)grid * 16);
+    cheb_long_kernel<RP><<<lgrid, 32 * kLongWarps, 0, g.stream>>>(a);
+    GP_LAUNCHED();
+  }
 }
 
 }  // namespace
@@ -262,7 +267,6 @@ static void run_single(Graph& g, const gp_request& req, gp_query_info* info, boo
   GP_CUDA_TRY(cudaMemsetAsync(w.y, 0, sizeof(float2) * g.n, g.stream));
   GP_CUDA_TRY(cudaMemsetAsync(w.norms, 0, sizeof(float) * (kPassCap + 2), g.stream));
   GP_CUDA_TRY(cudaMemsetAsync(w.state, 0, sizeof(int) * (kPassCap + 4), g.stream));
-  GP_CUDA_TRY(cudaMemsetAsync(g.sched.cnt, 0, sizeof(int) * std::max(g.sched.nlong, 1), g.stream));
   InitArgs ia;
   ia.rp = g.rp;
   ia.ci = g.ci;
@@ -288,7 +292,7 @@ static void run_single(Graph& g, const gp_request& req, gp_query_info* info, boo
   a.ntiles = g.sched.ntiles;
   a.poff = g.sched.poff;
   a.part = g.sched.part;
-  a.cnt = g.sched.cnt;
+  a.nlong = g.sched.nlong;
   a.hub = g.sched.hub;
   a.rp = g.rp;
   a.ci = g.ci;

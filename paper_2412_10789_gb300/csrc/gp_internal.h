@@ -89,8 +89,9 @@ struct DevBuf {
 //              have degree d = meta[9..18], so entry e belongs to row
 //              row0 + (e - e0) / d;
 //   chunk tile (meta bit 0 = 1): len = meta[1..10] entries of the long row row0,
-//              chunk index p = meta[11..31]; the warp that finishes a row's last
-//              chunk adds the chunks' partial sums in chunk order.
+//              chunk index p = meta[11..31]; the chunk's partial sum goes to
+//              slot poff[row0] + p, and a second kernel adds a row's partials
+//              in chunk order.
 // Warps claim tiles from a per-pass counter (all tiles move about the same
 // number of entries), double-buffering their indices with cp.async (step.cuh).
 #ifndef GP_STEP_THREADS
@@ -118,7 +119,6 @@ struct Schedule {
   int nlong = 0;           // long rows are relabelled rows 0..nlong-1
   int* poff = nullptr;     // device, nlong+1: first chunk slot of each long row
   float2* part = nullptr;  // device, per-chunk partial sums (hi, lo)
-  int* cnt = nullptr;      // device, chunks finished per long row (reset by the finisher)
   int hub = 0;             // rows 0..hub-1 of Q_k are cached in shared memory
   int smem_bytes = 0;      // dynamic shared memory of the step kernel
   int t_long = 0;          // rows of this degree or more are chunked

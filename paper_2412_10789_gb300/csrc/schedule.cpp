@@ -16,7 +16,7 @@ void build_schedule(Graph& g, const std::vector<int64_t>& rp) {
     tiles.push_back(make_int4((int)row, (int)(uint32_t)(e0 & 0xffffffffLL), (int)(e0 >> 32), (int)meta));
   };
   // Long rows (more entries than a tile, or at least cfg.t_heavy): chunks of
-  // kTileCap entries, combined by the warp that finishes the row's last chunk.
+  // kTileCap entries, whose partial sums the long-row kernel combines.
   const int64_t t_long = g.cfg.t_heavy > 0 ? std::min<int64_t>(g.cfg.t_heavy, kTileCap + 1) : kTileCap + 1;
   int64_t row = 0;
   while (row < na && deg(row) >= t_long) {
@@ -64,12 +64,10 @@ void build_schedule(Graph& g, const std::vector<int64_t>& rp) {
   s.tiles = (int4*)A->get(sizeof(int4) * std::max<size_t>(tiles.size(), 1));
   s.poff = (int*)A->get(sizeof(int) * poff.size());
   s.part = (float2*)A->get(sizeof(float2) * std::max(poff.back(), 1));
-  s.cnt = (int*)A->get(sizeof(int) * std::max(nlong, 1));
   if (!tiles.empty())
     GP_CUDA_TRY(cudaMemcpyAsync(s.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
                                 g.stream));
   GP_CUDA_TRY(cudaMemcpyAsync(s.poff, poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice, g.stream));
-  GP_CUDA_TRY(cudaMemsetAsync(s.cnt, 0, sizeof(int) * std::max(nlong, 1), g.stream));
   GP_CUDA_TRY(cudaStreamSynchronize(g.stream));
 }
 
@@ -78,7 +76,6 @@ void free_schedule(Graph& g) {
   g.alloc.put(s.tiles);
   g.alloc.put(s.poff);
   g.alloc.put(s.part);
-  g.alloc.put(s.cnt);
   s = Schedule{};
 }
 

@@ -13,7 +13,9 @@
 // runs of equal-degree rows, or chunks of one long row.  Warps claim tiles
 // from a per-pass counter; each warp double-buffers tile indices in shared memory, copying
 // the next tile's col_idx with 16-byte cp.async while it gathers and sums the
-// current one.  Gathers of indices below `hub` read a shared-memory copy of
+// current one.  A chunk of a long row only stores its partial sum; a second,
+// small kernel (cheb_long_kernel) adds each long row's partials in chunk order
+// and updates the row, so the step needs no fences or counters between warps.  Gathers of indices below `hub` read a shared-memory copy of
 // the hub rows of Q_k (the most gathered values); the rest go to L2.  The
 // kernel is persistent: one CTA of kStepThreads threads per SM.
 #pragma once
@@ -35,8 +37,8 @@ struct StepArgs {
   int* state;          // [0] = stop K, [2 + k] = tiles claimed in pass k
   const int* poff;     // long rows: first chunk slot
   float2* part;        // long rows: chunk partial sums
-  int* cnt;            // long rows: chunks finished
   int hub;             // rows of Q_k cached in shared memory
+  int nlong;           // long (chunked) rows: relabelled rows 0..nlong-1
   int k;               // this pass computes r_{k+1}
   float c_hi, c_lo;    // c_{k+1} as a float pair
   float tail;          // tail(k) (stop test), negative disables the test
@@ -244,31 +246,65 @@ __device__ __forceinline__ void finish_rows(Ctx& c, const TileInfo& t, int* idx)
   }
 }
 
-// Chunk of a long row: sum it, store the partial; the warp that finishes the
-// row's last chunk adds the partials in chunk order (lane i takes chunks i,
-// i+32, ...; then a fixed shuffle tree), so the result does not depend on which
-// warp finishes.
-template <typename RP>
+// Chunk of a long row: sum it and store the partial (slot poff[row] + p).
 __device__ __forceinline__ void finish_chunk(Ctx& c, const TileInfo& t, const int* idx) {
   const StepArgs& a = *c.a;
-  const RP* rp = (const RP*)a.rp;
   const int lane = threadIdx.x & 31;
   const int off0 = (int)(t.e0 & 3);
   KSum s{0.f, 0.f};
   gather_sum<GP_GATHER_N>(c, idx, off0 + lane, 32, (t.len - lane + 31) / 32, s);
   const DF v = shfl_sum_df(ksum_value(s), 32);
-  const int64_t row = t.row0;
-  const int slot0 = a.poff[row];
-  const int np = a.poff[row + 1] - slot0;
-  int old = 0;
-  if (lane == 0) {
-    a.part[slot0 + t.p] = make_float2(v.hi, v.lo);
-    __threadfence();
-    old = atomicAdd(&a.cnt[row], 1);
+  if (lane == 0) a.part[a.poff[t.row0] + t.p] = make_float2(v.hi, v.lo);
+}
+
+// The stop test at the top of pass k: stop once tail(k) * max_{l<=k} ||r_l||_1
+// <= tol (Theorem 1 with the measured C).  Thread-local; the caller shares it.
+__device__ __forceinline__ int pass_stopped(const StepArgs& a) {
+  if (a.tail < 0.f) return 0;
+  float C = 0.f;
+  for (int l = 0; l <= a.k; ++l) C = fmaxf(C, a.norms[l]);
+  return a.tail * C <= a.tol;
+}
+
+// Block sum of the warps' ||r_{k+1}||_1 partials, one atomic per CTA.
+template <int W>
+__device__ __forceinline__ void add_norm(const StepArgs& a, float nrm, float* s_norm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+  if (lane == 0) s_norm[warp] = nrm;
+  __syncthreads();
+  if (warp == 0) {
+    float w = lane < W ? s_norm[lane] : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+    if (lane == 0 && w != 0.f) atomicAdd(&a.norms[a.k + 1], w);
   }
-  old = __shfl_sync(0xffffffffu, old, 0);
-  if (old == np - 1) {
-    __threadfence();
+}
+
+// Long rows after the step: one warp per row adds the row's chunk partials in
+// chunk order (lane i takes chunks i, i+32, ...; then a fixed shuffle tree), so
+// the sum does not depend on which warp stored which chunk, and applies the
+// row update.  Runs after cheb_step_kernel on the same stream and before the
+// next pass, whose shared-memory hub reads these rows of Q_{k+1}.
+constexpr int kLongWarps = 8;
+template <typename RP>
+__global__ void __launch_bounds__(32 * kLongWarps) cheb_long_kernel(const __grid_constant__ StepArgs a) {
+  __shared__ int s_flag;
+  __shared__ float s_norm[kLongWarps];
+  if (threadIdx.x == 0) s_flag = pass_stopped(a);
+  __syncthreads();
+  if (s_flag) return;
+  const RP* rp = (const RP*)a.rp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Ctx c;
+  c.a = &a;
+  c.hub_q = nullptr;
+  c.nrm = 0.f;
+  for (int64_t row = (int64_t)blockIdx.x * kLongWarps + warp; row < a.nlong;
+       row += (int64_t)gridDim.x * kLongWarps) {
+    const int slot0 = a.poff[row];
+    const int np = a.poff[row + 1] - slot0;
     DF acc{0.f, 0.f};
     for (int i = lane; i < np; i += 32) {
       const float2 pv = __ldcg(a.part + slot0 + i);
@@ -276,12 +312,12 @@ __device__ __forceinline__ void finish_chunk(Ctx& c, const TileInfo& t, const in
     }
     acc = shfl_sum_df(acc, 32);
     if (lane == 0) {
-      a.cnt[row] = 0;
       const float qp = a.cheb ? ld_own(a.qprev + row) : 0.f;
       const float2 yv = ld_own2(a.y + row);
       row_update(c, row, (int64_t)(rp[row + 1] - rp[row]), acc, qp, yv);
     }
   }
+  add_norm<kLongWarps>(a, c.nrm, s_norm);
 }
 
 template <typename RP>
@@ -290,13 +326,8 @@ __global__ void __launch_bounds__(kStepThreads, 1) cheb_step_kernel(const __grid
   __shared__ int s_flag;
   __shared__ float s_norm[kStepWarps];
   if (threadIdx.x == 0) {
-    int stop = 0;
-    if (a.tail >= 0.f) {
-      float C = 0.f;
-      for (int l = 0; l <= a.k; ++l) C = fmaxf(C, a.norms[l]);
-      stop = a.tail * C <= a.tol;
-      if (stop && blockIdx.x == 0) atomicMin(&a.state[0], a.k);
-    }
+    const int stop = pass_stopped(a);
+    if (stop && blockIdx.x == 0) atomicMin(&a.state[0], a.k);
     s_flag = stop;
   }
   __syncthreads();
@@ -310,62 +341,59 @@ __global__ void __launch_bounds__(kStepThreads, 1) cheb_step_kernel(const __grid
   c.pol_stream = policy_evict_first();
   c.pol_keep = policy_evict_last();
   c.nrm = 0.f;
+  // Tiles: each warp starts with tiles w, w + W and w + 2W (W warps in the
+  // grid), then claims the next unclaimed tile from this pass's counter
+  // (state[2 + k], zeroed per query), so no warp is left with a run of costly
+  // tiles at the end.  The claim is three tiles ahead: its atomic and the load
+  // of its descriptor complete while the warp works on the current tile.
   const int64_t stride = (int64_t)gridDim.x * kStepWarps;
   int64_t t = (int64_t)blockIdx.x * kStepWarps + warp;
-  // stage the first tile's indices, then fill the hub while they land
+  int64_t tn = t + stride, tnn = t + 2 * stride;
   TileInfo cur{};
   if (t < a.ntiles) {
     cur = decode(a.tiles[t]);
     stage_indices(c, cur, wbase);
   }
   cp_async_commit();
+  int4 dn = make_int4(0, 0, 0, 0);  // descriptor of tile tn
+  if (tn < a.ntiles) dn = a.tiles[tn];
+  // fill the hub while the first tile's indices land
   {
     const float4* src = reinterpret_cast<const float4*>(a.qcur);
     float4* dst = reinterpret_cast<float4*>(hub_q);
     for (int i = threadIdx.x; i < a.hub / 4; i += kStepThreads) dst[i] = __ldcg(src + i);
   }
   __syncthreads();
-  // Each warp starts with tiles t and t + stride, then claims the next
-  // unclaimed tile from this pass's counter (state[2 + k], zeroed per query)
-  // one tile ahead, so no warp is left with a run of costly tiles at the end.
-  int64_t tn = t + stride;
   int b = 0;
   while (t < a.ntiles) {
     TileInfo nxt{};
     if (tn < a.ntiles) {
-      nxt = decode(a.tiles[tn]);
+      nxt = decode(dn);
       stage_indices(c, nxt, wbase + (b ^ 1) * kTileSpan);
     }
-    int64_t tnn = 0;
-    if (lane == 0) tnn = 2 * stride + atomicAdd(&a.state[2 + a.k], 1);
-    tnn = __shfl_sync(0xffffffffu, tnn, 0);
     cp_async_commit();
+    int claimed = 0;
+    if (lane == 0) claimed = atomicAdd(&a.state[2 + a.k], 1);
+    int4 dnn = make_int4(0, 0, 0, 0);
+    if (tnn < a.ntiles) dnn = a.tiles[tnn];
     cp_async_wait<1>();  // this lane's copies of tile t have landed
     __syncwarp();        // ... and every lane's
     int* idx = wbase + b * kTileSpan;
     if (cur.kind == 0)
       finish_rows(c, cur, idx);
     else
-      finish_chunk<RP>(c, cur, idx);
+      finish_chunk(c, cur, idx);
     __syncwarp();  // the buffer is free for the copy two tiles ahead
+    const int64_t t3 = 3 * stride + __shfl_sync(0xffffffffu, claimed, 0);
     cur = nxt;
     b ^= 1;
     t = tn;
     tn = tnn;
+    tnn = t3;
+    dn = dnn;
   }
   cp_async_wait<0>();
-  // ||r_{k+1}||_1: warp sums, block sum, one atomic per CTA
-  float nrm = c.nrm;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
-  if (lane == 0) s_norm[warp] = nrm;
-  __syncthreads();
-  if (warp == 0) {
-    float w = lane < kStepWarps ? s_norm[lane] : 0.f;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
-    if (lane == 0 && w != 0.f) atomicAdd(&a.norms[a.k + 1], w);
-  }
+  add_norm<kStepWarps>(a, c.nrm, s_norm);
 }
 
 }  // namespace
