@@ -66,6 +66,8 @@ def parse():
                    help="rmat22: the headline single-source workload; the others time the batched and "
                         "served forms on the larger graphs")
     p.add_argument("--requests", type=int, default=10000, help="chunglu24_serve: requests per load level")
+    p.add_argument("--serve-width", type=int, default=512,
+                   help="chunglu24_serve: query slots of the service block (a power of two, <= 512)")
     p.add_argument("--loads", default="0.5,0.8,0.95", help="chunglu24_serve: offered load levels")
     return p.parse_args()
 
@@ -529,8 +531,8 @@ def serve_poisson(gp, g, dev, args):
     fns = rng.integers(0, 2, nreq)
     params = [(0.1, 0.2, 0.5)[k] if f == 0 else (3.0, 5.0, 10.0)[k] for f, k in zip(fns, rng.integers(0, 3, nreq))]
     tols = rng.choice([1e-4, 1e-5, 1e-6], nreq)
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=256)
-    pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range(512)]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=args.serve_width)
+    pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range(args.serve_width + 64)]
     free = list(range(len(pool)))
 
     def run(arrivals):
@@ -664,7 +666,7 @@ def run_workload(args, rank, world):
         queries, forms, width, headline = None, None, 128, None
     else:
         g = gg.chung_lu(1 << 24, 30.0, 2.1, seed=4)
-        queries, forms, width, headline = None, None, 256, None
+        queries, forms, width, headline = None, None, args.serve_width, None
     t_gen = time.perf_counter() - t_gen
     sampler.start()
     if args.workload == "rmat22_push":

@@ -11,8 +11,9 @@
  * (Lemma 1, coefficients of Lemma 2 / Lemma 3) with the three-term recurrence
  * r_{k+1} = 2 P r_k - r_{k-1} (Eq. res-recurrence, Algorithm 3), accumulating
  * y += c_k r_k in the same pass.  K is the smallest k >= 1 with
- * tail(k) * max_{l<=k} ||r_l||_1 <= l1_tol, tail(k) = sum_{l>k} |c_l| (Theorem 1
- * read for the l1 error with Assumption 1's constant measured on the fly), or
+ * tail(k) * 2 max_{l<=k} ||r_l||_1 <= l1_tol, tail(k) = sum_{l>k} |c_l| (Theorem 1
+ * read for the l1 error with Assumption 1's constant estimated on the fly:
+ * twice the largest norm so far, since ||r_k||_1 can still grow after k), or
  * a cap.  A node with d_u = 0 has a zero column in P; an isolated source
  * returns f(0) e_s.
  *
@@ -60,7 +61,7 @@ typedef enum { GP_F32 = 0, GP_F64 = 1, GP_BF16 = 2, GP_F16 = 3 } gp_dtype;
 typedef enum { GP_FN_PPR = 0, GP_FN_HKPR = 1 } gp_function;
 
 typedef enum {
-  GP_K_TAIL = 0,  /* stop at tail(k) * max_l ||r_l||_1 <= l1_tol (default) */
+  GP_K_TAIL = 0,  /* stop at tail(k) * 2 max_{l<=k} ||r_l||_1 <= l1_tol (default) */
   GP_K_PAPER = 1, /* K = ceil(alpha^{-1/2} ln(1/tol)) or ceil(sqrt(t) ln(1/tol)) (Section 6) */
   GP_K_FIXED = 2  /* K = gp_request.k_fixed */
 } gp_k_rule;
@@ -93,7 +94,7 @@ typedef struct {
 typedef struct {
   int32_t K;             /* truncation degree used (number of applications of P) */
   int32_t k16_from;      /* first step stored in 16 bits (K+1 when none) */
-  double tail_bound;     /* tail(K) * max_{l<=K} ||r_l||_1, the l1 bound of the stop rule */
+  double tail_bound;     /* tail(K) * 2 max_{l<=K} ||r_l||_1, the l1 bound of the stop rule */
   double max_r_l1;       /* max_{l<=K} ||r_l||_1 as measured on the device */
   double ms;             /* wall time of the query inside the library, milliseconds */
 } gp_query_info;
@@ -248,8 +249,8 @@ gp_status gp_ppr_bidirectional(gp_graph* g, int32_t source, double alpha, double
 /*
  * Autotuner for the batched form (the block width B; the paper has no
  * counterpart).  Times fused SpMM passes of the column engine on this graph at
- * each candidate width (powers of two in [8, 256]; widths == NULL means 32,
- * 64, 128, 256) with CUDA events on the graph's stream, for `storage` (16-bit
+ * each candidate width (powers of two in [8, 256]; widths == NULL means 8,
+ * 16, 32, 64, 128, 256) with CUDA events on the graph's stream, for `storage` (16-bit
  * storage: 0.45 of an FP32 warm-up pass plus 0.55 of a 16-bit pass), and
  * returns the width with the least device time per column and pass in
  * *best_width, and that time in microseconds in *us_per_column_pass
@@ -269,7 +270,11 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
  * the memory for its share of the block are free, advances every active column
  * one step per fused SpMM pass, retires a column when its stop rule fires
  * (writing y_out before the ticket completes) and refills the slot.  The
- * request's y_out must stay valid until gp_poll reports completion.
+ * block has as many slots as the memory budget allows (cfg.mem_budget, default
+ * 80% of the free device memory), at most cfg.block_width (0: 512), a power of
+ * two; a block wider than 256 columns runs as 256-column halves, each with its
+ * own pass.  The request's y_out must stay valid until gp_poll reports
+ * completion.
  * gp_poll returns GP_OK (and fills info) once the ticket is done, GP_EAGAIN
  * before that, GP_ENOTFOUND for an unknown or already-collected ticket.
  */
@@ -277,7 +282,8 @@ gp_status gp_submit(gp_graph* g, const gp_request* req, uint64_t* ticket);
 gp_status gp_poll(gp_graph* g, uint64_t ticket, gp_query_info* info);
 
 /* Serving statistics since the graph was created: completed queries, steps
- * (fused passes) run, and the mean number of active columns per pass. */
+ * run (one fused pass over each block half that has active columns), and the
+ * mean number of active columns per step. */
 gp_status gp_serve_stats(gp_graph* g, uint64_t* completed, uint64_t* steps, double* mean_active);
 
 /*

@@ -194,7 +194,7 @@ def chebypower(g, s_or_x, kind, param: float, K: int, coeffs: np.ndarray | None 
 
 
 def chebypower_tol(g, s_or_x, kind, param: float, tol: float, Kmax: int = 200):
-    """Algorithm 3 stopping at the smallest K with tail(K) * max_{l<=K} ||r_l||_1 <= tol.
+    """Algorithm 3 stopping at the smallest K with tail(K) * 2 max_{l<=K} ||r_l||_1 <= tol.
 
     Returns (y, K, norms[0..K])."""
     c = cheb_coeffs(kind, param, Kmax)

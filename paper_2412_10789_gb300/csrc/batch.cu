@@ -298,7 +298,7 @@ struct SpmmArgs {
   int B;                // columns of this pass (a prefix of each row)
   int ldb;              // row stride of the blocks, in elements
   int check;            // col_idx lists rows beyond the active ones (host: picks the kernel)
-  int* tile_ctr;        // tiles claimed past the first two per warp (zeroed by the control kernel)
+  int* tile_ctr;        // tiles claimed past the first three per warp (zeroed by the control kernel)
   int mode;             // kModeForward, kModeClenshaw or kModeClenshawFinal
 };
 
@@ -370,6 +370,45 @@ __device__ __forceinline__ void add_seg(const unsigned char* p, float acc[LC]) {
 #pragma unroll
   for (int h = 0; h < LC / 8; ++h) Store<TG>::add(Store<TG>::lds(p + h * 8 * Store<TG>::bytes), acc + 8 * h);
 }
+
+// A lane's neighbour sums.  FP32 gathers add in two levels: rounds go into
+// blk, and every kBlk rounds (a warp-uniform count kept by the loop) blk is
+// added to acc, so the rounding error of a lane's sum over n entries grows
+// like kBlk + n / kBlk ulps instead of n (a lane of a 256-column FP32 pass sums
+// a whole 508-entry chunk).  16-bit gathers carry their own storage rounding,
+// far above that, and add directly.
+constexpr int kBlk = 16;
+template <typename TG, int LC>
+struct LaneSum {
+  static constexpr bool kTwo = Store<TG>::bytes == 4;
+  float acc[LC];
+  float blk[kTwo ? LC : 1];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+    if constexpr (kTwo) {
+#pragma unroll
+      for (int i = 0; i < LC; ++i) blk[i] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void add(const unsigned char* p) { add_seg<TG, LC>(p, kTwo ? blk : acc); }
+  // after round r of a sum (warp-uniform r): close a block every kBlk rounds
+  __device__ __forceinline__ void round_done(int r) {
+    if constexpr (kTwo) {
+      if ((r & (kBlk - 1)) == kBlk - 1) flush();
+    }
+  }
+  // acc = the whole sum (call before acc is read)
+  __device__ __forceinline__ void flush() {
+    if constexpr (kTwo) {
+#pragma unroll
+      for (int i = 0; i < LC; ++i) {
+        acc[i] += blk[i];
+        blk[i] = 0.f;
+      }
+    }
+  }
+};
 
 // Copy a tile's col_idx entries [e0, e0 + len) into a warp's staging buffer
 // with 16-byte copies from the aligned-down start; entry e0 + i lands at
@@ -522,9 +561,8 @@ __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& 
     }
     p_off = (p_off + C::kStride) & C::kMask;
   };
-  float acc[LC];
-#pragma unroll
-  for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+  LaneSum<TG, LC> sum;
+  sum.zero();
 #pragma unroll 1
   for (int i = 0; i < S - 1; ++i) {
     issue();
@@ -538,14 +576,17 @@ __device__ __forceinline__ void tile_rows_per_group(const Lane& L, const BTile& 
     const unsigned char* src = L.ring_p + c_off;
     const bool mine = c_row < nrows;
     if (c_left > 0) {
-      if (mine) add_seg<TG, LC>(src, acc);
+      if (mine) sum.add(src);
+      sum.round_done(d - c_left);
       --c_left;
     } else {
-      if (c_own == 0) Store<TG>::template finish<LC>(acc);
-      if (mine) own_round<TP, TO, LC, SB, OP, C::OY>(L, t.row0 + c_row, (float)d, c_own, src, acc, nrm);
+      if (c_own == 0) {
+        sum.flush();
+        Store<TG>::template finish<LC>(sum.acc);
+      }
+      if (mine) own_round<TP, TO, LC, SB, OP, C::OY>(L, t.row0 + c_row, (float)d, c_own, src, sum.acc, nrm);
       if (++c_own == OWN) {
-#pragma unroll
-        for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+        sum.zero();
         c_own = 0;
         c_row += EG;
         c_left = d;
@@ -660,9 +701,8 @@ __device__ __forceinline__ void tile_chunk(const Lane& L, const BTile& t, const 
     pj += EG;
     p_off = (p_off + C::kStride) & C::kMask;
   };
-  float acc[LC];
-#pragma unroll
-  for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+  LaneSum<TG, LC> sum;
+  sum.zero();
 #pragma unroll 1
   for (int i = 0; i < S - 1; ++i) {
     issue();
@@ -675,8 +715,9 @@ __device__ __forceinline__ void tile_chunk(const Lane& L, const BTile& t, const 
     bwait<S - 3>();  // rounds rc and rc + 1 have landed
     const unsigned char* s0 = L.ring_p + c_off;
     const unsigned char* s1 = L.ring_p + ((c_off + C::kStride) & C::kMask);
-    if (cj < len) add_seg<TG, LC>(s0, acc);
-    if (cj + EG < len) add_seg<TG, LC>(s1, acc);
+    if (cj < len) sum.add(s0);
+    if (cj + EG < len) sum.add(s1);
+    sum.round_done(rc + 1);
     cj += 2 * EG;
     c_off = (c_off + 2 * C::kStride) & C::kMask;
     issue();
@@ -686,11 +727,12 @@ __device__ __forceinline__ void tile_chunk(const Lane& L, const BTile& t, const 
   }
   if (rc < G) {
     bwait<S - 2>();
-    if (cj < len) add_seg<TG, LC>(L.ring_p + c_off, acc);
+    if (cj < len) sum.add(L.ring_p + c_off);
     issue();
     bcommit();
   }
-  publish_chunk<TG, TP, TO, LC>(L, t, acc, nrm);
+  sum.flush();
+  publish_chunk<TG, TP, TO, LC>(L, t, sum.acc, nrm);
 }
 
 // Kind 1 tile: the EG lane groups split each row's entries (entry j of a row
@@ -730,9 +772,8 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
     }
     p_off = (p_off + C::kStride) & C::kMask;
   };
-  float acc[LC];
-#pragma unroll
-  for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+  LaneSum<TG, LC> sum;
+  sum.zero();
 #pragma unroll 1
   for (int i = 0; i < S - 1; ++i) {
     issue();
@@ -745,18 +786,19 @@ __device__ __forceinline__ void tile_rows_per_warp(const Lane& L, const BTile& t
     bwait<S - 2>();  // round rc has landed
     const unsigned char* src = L.ring_p + c_off;
     if (c_left > 0) {
-      if (c_j < d) add_seg<TG, LC>(src, acc);
+      if (c_j < d) sum.add(src);
+      sum.round_done(G - c_left);
       c_j += EG;
       --c_left;
     } else {
       if (c_own == 0) {  // the row's sums, before its first own piece
-        reduce_groups<LC>(acc, L.CG);
-        Store<TG>::template finish<LC>(acc);
+        sum.flush();
+        reduce_groups<LC>(sum.acc, L.CG);
+        Store<TG>::template finish<LC>(sum.acc);
       }
-      if (g == 0) own_round<TP, TO, LC, SB, OP, C::OY>(L, t.row0 + c_seq, (float)d, c_own, src, acc, nrm);
+      if (g == 0) own_round<TP, TO, LC, SB, OP, C::OY>(L, t.row0 + c_seq, (float)d, c_own, src, sum.acc, nrm);
       if (++c_own == OWN) {
-#pragma unroll
-        for (int i = 0; i < LC; ++i) acc[i] = 0.f;
+        sum.zero();
         c_own = 0;
         ++c_seq;
         c_left = G;
@@ -815,12 +857,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
 #pragma unroll
   for (int i = 0; i < LC; ++i) nrm[i] = 0.f;
 
-  // Tiles: each warp starts with tiles w and w + nwarps, then takes the next
-  // unclaimed tile from a per-pass counter one tile ahead, so the pass ends
-  // when the work does rather than with the warp that drew the costliest tiles.
+  // Tiles: each warp starts with tiles w, w + W and w + 2W (W warps in the
+  // grid), then takes the next unclaimed tile from a per-pass counter, so the
+  // pass ends when the work does rather than with the warp that drew the
+  // costliest tiles.  A claim is three tiles ahead: its atomic completes while
+  // the warp works on the current tile, and the claimed tile's descriptor
+  // loads during the next one.
   const int64_t nwarps = (int64_t)gridDim.x * kBatchWarps;
   int64_t w = (int64_t)blockIdx.x * kBatchWarps + warp;
-  int64_t wn = w + nwarps;
+  int64_t wn = w + nwarps, wnn = w + 2 * nwarps;
   int4 cur = make_int4(0, 0, 0, 0), nd = make_int4(0, 0, 0, 0);
   if (w < a.ntiles) {
     cur = a.tiles[w];
@@ -838,9 +883,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
       const BTile tn = decode_btile(nd);
       stage_indices(s_ci + (buf ^ 1) * kBTileSpan, a.ci, tn.e0, tile_len(tn), lane);
     }
-    int64_t wnn = 0;
-    if (lane == 0) wnn = 2 * nwarps + atomicAdd(a.tile_ctr, 1);
-    wnn = __shfl_sync(0xffffffffu, wnn, 0);
+    int claimed = 0;
+    if (lane == 0) claimed = atomicAdd(a.tile_ctr, 1);
     int4 nd2 = make_int4(0, 0, 0, 0);
     if (wnn < a.ntiles) nd2 = a.tiles[wnn];
     if (t.kind == 0)
@@ -849,10 +893,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
       tile_rows_per_warp<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
     else
       tile_chunk<TG, TP, TO, LC, CHECK>(L, t, ci_t, nrm);
+    const int64_t w3 = 3 * nwarps + __shfl_sync(0xffffffffu, claimed, 0);
     cur = nd;
     nd = nd2;
     w = wn;
     wn = wnn;
+    wnn = w3;
     bwait<0>();  // only empty groups remain; the next tile restarts the ring at slot 0
   }
 #pragma unroll
@@ -1296,7 +1342,7 @@ std::vector<int> ColumnEngine::admit(const std::vector<gp_request>& reqs, std::v
       p.c[k] = (float)c[k];
       p.tail[k] = (float)tail[k];
     }
-    p.tol = r.k_rule == GP_K_TAIL ? (float)r.l1_tol : -1.0f;
+    p.tol = r.k_rule == GP_K_TAIL ? (float)(r.l1_tol / kCMargin) : -1.0f;
     p.kstop = r.k_rule == GP_K_FIXED ? r.k_fixed
               : r.k_rule == GP_K_PAPER ? std::min(kcap - 1, paper_k(r.function, r.param, r.l1_tol))
                                        : 0;
@@ -1446,7 +1492,7 @@ std::vector<ColumnEngine::Finished> ColumnEngine::collect(bool force_all) {
     f.req = slots_[j].req;
     f.K = stat[j].done ? stat[j].K : stat[j].k;
     f.C = stat[j].C;
-    f.tail_bound = (double)slots_[j].tails[std::min(f.K, kMaxColK - 1)] * stat[j].C;
+    f.tail_bound = kCMargin * (double)slots_[j].tails[std::min(f.K, kMaxColK - 1)] * stat[j].C;
     f.t_admit = slots_[j].t_admit;
     f.k16_from = h_pass_ >= 0 ? h_pass_ : f.K + 1;
     fin.push_back(f);
@@ -1802,7 +1848,7 @@ int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_
       if (us_out) *us_out = it->second.second;
       return it->second.first;
     }
-    widths = {32, 64, 128, 256};
+    widths = {8, 16, 32, 64, 128, 256};
   }
   std::vector<int32_t> srcs;
   for (int64_t u = 0; u < g.n && (int)srcs.size() < 256; ++u)
@@ -2100,7 +2146,7 @@ std::vector<ColumnEngine::Finished> ColumnEngine::propagate(const float* X, floa
     p.c[k] = (float)c[k];
     p.tail[k] = (float)tail[k];
   }
-  p.tol = (float)tol;
+  p.tol = (float)(tol / kCMargin);
   p.kstop = 0;
   p.warm = 0;
   for (int k = 0; k <= kcap_ && k < kMaxColK; ++k)

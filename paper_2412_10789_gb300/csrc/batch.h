@@ -23,7 +23,7 @@ struct ColState {
 struct ColParam {
   float c[kMaxColK];     // Chebyshev coefficients c_0..
   float tail[kMaxColK];  // tail(k) = sum_{l>k} |c_l|
-  float tol;             // l1 tolerance of the stop rule (< 0: no rule)
+  float tol;             // l1 tolerance over kCMargin: stop at tail(k) * C <= tol (< 0: no rule)
   int kstop;             // fixed K (> 0) or 0
   int warm;              // first k with tail(k) < warmup_tail
   int pad;

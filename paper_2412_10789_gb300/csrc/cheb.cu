@@ -249,14 +249,14 @@ static void run_single(Graph& g, const gp_request& req, gp_query_info* info, boo
   if (use_precise(g)) {
     // tiny graph: float-pair storage of Q (precise.cu)
     double C = 1.0;
-    const int K = run_precise(g, s, cheb, c, tail, cheb ? k_fixed : (int)c.size() - 1, req.l1_tol, kcap, &C);
+    const int K = run_precise(g, s, cheb, c, tail, cheb ? k_fixed : (int)c.size() - 1, req.l1_tol / kCMargin, kcap, &C);
     emit_output(g, req, false, f0);
     if (sync_needed) GP_CUDA_TRY(cudaStreamSynchronize(g.stream));
     if (info) {
       info->K = K;
       info->k16_from = K + 1;
       info->max_r_l1 = cheb ? C : 1.0;
-      info->tail_bound = cheb && K < (int)tail.size() ? tail[K] * C : 0.0;
+      info->tail_bound = cheb && K < (int)tail.size() ? kCMargin * tail[K] * C : 0.0;
       info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     return;
@@ -299,7 +299,7 @@ static void run_single(Graph& g, const gp_request& req, gp_query_info* info, boo
   a.y = w.y;
   a.norms = w.norms;
   a.state = w.state;
-  a.tol = (float)req.l1_tol;
+  a.tol = (float)(req.l1_tol / kCMargin);
   a.cheb = cheb ? 1 : 0;
   const int grid = step_grid(g);
   float* bufs[2] = {w.qa, w.qb};  // bufs[k & 1] holds Q_k
@@ -337,7 +337,7 @@ static void run_single(Graph& g, const gp_request& req, gp_query_info* info, boo
   } else {
     // Stop rule: no stop is possible before k_lo (max ||r_l||_1 >= ||r_0||_1 = 1);
     // launch up to k_lo + chunk, then read K back and continue if needed.
-    int k_lo = k_lower(tail, req.l1_tol, 1.0);
+    int k_lo = k_lower(tail, req.l1_tol / kCMargin, 1.0);
     const int chunk = 6;
     int k = 1;
     int limit = std::min(kcap - 1, k_lo + chunk);
@@ -379,7 +379,7 @@ static void run_single(Graph& g, const gp_request& req, gp_query_info* info, boo
     info->k16_from = K_done + 1;
     info->max_r_l1 = cheb ? C : 1.0;
     if (cheb) {
-      info->tail_bound = Kr < (int)tail.size() ? tail[Kr] * C : 0.0;
+      info->tail_bound = Kr < (int)tail.size() ? kCMargin * tail[Kr] * C : 0.0;
     } else {
       double t = 0.0;  // Taylor tail beyond the N terms used, ||P^k e_s||_1 = 1
       std::vector<double> zall;

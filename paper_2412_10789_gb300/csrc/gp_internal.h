@@ -63,6 +63,13 @@ int paper_k(int function, double param, double tol);
 // Smallest k with tail[k] * cmin <= tol (cmin = 1 is the least possible
 // max ||r_l||_1), used to size the launch sequence.
 int k_lower(const std::vector<double>& tail, double tol, double cmin);
+// The l1 stop rule (Theorem 1 with Assumption 1's C estimated on the fly):
+// stop at the smallest k with tail(k) * kCMargin * max_{l<=k} ||r_l||_1 <= tol.
+// ||r_k||_1 can still grow after k (on power-law graphs the running maximum
+// alone let the truncation pass tol by a few percent); the first omitted term
+// obeys ||r_{k+1}||_1 <= 2 ||P r_k||_1 + ||r_{k-1}||_1 <= 3 max_{l<=k} ||r_l||_1,
+// P being column-stochastic, and the margin read here is 2.
+constexpr double kCMargin = 2.0;
 
 // ----------------------------------------------------------------- device memory
 

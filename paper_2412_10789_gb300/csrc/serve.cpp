@@ -1,15 +1,17 @@
 // Continuous-batching service (gp_submit / gp_poll / gp_serve_stats).
 //
-// One service thread per graph owns a column engine (batch.h) on its own
-// stream.  Its width (columns = query slots) is what the memory budget allows
-// (cfg.mem_budget, default 80% of the free device memory, at
-// ColumnEngine::bytes_per_column each, capped by cfg.block_width or 256), so a
-// free column is also free memory for one more query.  Each iteration admits
-// queued requests into free columns, runs one fused pass over all active
-// columns (the per-column stop rule runs on the device in the pass's control
-// kernel), and every few passes collects the retired columns: their y is
-// written to the request's y_out, the ticket completes, and the column is free
-// for the next request.  Passes cover only the prefix of columns that holds
+// One service thread per graph owns the column engines (batch.h) of its block
+// on its own stream.  The block's width (columns = query slots) is what the
+// memory budget allows (cfg.mem_budget, default 80% of the free device memory,
+// at ColumnEngine::bytes_per_column each, capped by cfg.block_width or 512),
+// so a free column is also free memory for one more query.  A warp spans at
+// most 256 FP32 columns of a row, so a 512-column block is two 256-column
+// engines, each advanced by its own fused pass.  Each iteration admits queued
+// requests into free columns (first engine first), runs one fused pass over
+// the active columns of each engine that has any (the per-column stop rule
+// runs on the device in the pass's control kernel), and every few passes
+// collects the retired columns: their y is written to the request's y_out,
+// the ticket completes, and the column is free for the next request.  Passes cover only the prefix of columns that holds
 // the busy ones, and the busy columns are moved to the front when at most
 // half of that prefix is busy, so a lightly loaded service runs narrow passes.  Requests therefore join and leave the running block
 // while the others keep going; their work shares every pass.
@@ -29,6 +31,8 @@ namespace gp {
 namespace {
 
 constexpr size_t kQueueCap = 1 << 20;
+constexpr int kServeMaxWidth = 512;   // query slots of the service's block
+constexpr int kEngineMaxWidth = 256;  // columns of one engine
 constexpr int kCollectEvery = 2;
 
 struct Ticket {
@@ -46,7 +50,7 @@ struct Serve {
   Graph* g = nullptr;
   int device = 0;
   cudaStream_t stream = nullptr;
-  std::unique_ptr<ColumnEngine> eng;
+  std::vector<std::unique_ptr<ColumnEngine>> engs;  // the block's column halves
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Ticket> pending;
@@ -58,6 +62,17 @@ struct Serve {
   std::thread th;
   uint64_t completed = 0, passes = 0;
   double active_sum = 0.0;
+
+  int active() const {
+    int a = 0;
+    for (const auto& e : engs) a += e->active();
+    return a;
+  }
+  int free_slots() const {
+    int f = 0;
+    for (const auto& e : engs) f += e->free_slots();
+    return f;
+  }
 
   void run() {
     cudaSetDevice(device);
@@ -89,9 +104,9 @@ struct Serve {
       std::vector<uint64_t> tags;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv.wait(lk, [&] { return stop || !pending.empty() || eng->active() > 0; });
+        cv.wait(lk, [&] { return stop || !pending.empty() || active() > 0; });
         if (stop) return;
-        int free = eng->free_slots();
+        int free = free_slots();
         while (free > 0 && !pending.empty()) {
           Ticket t = pending.front();
           pending.pop_front();
@@ -101,24 +116,33 @@ struct Serve {
           --free;
         }
       }
-      if (!reqs.empty()) {
-        std::vector<int> slots = eng->admit(reqs, tags);
+      for (size_t e = 0, i = 0; e < engs.size() && i < reqs.size(); ++e) {
+        const size_t take = std::min(reqs.size() - i, (size_t)engs[e]->free_slots());
+        if (take == 0) continue;
+        std::vector<gp_request> r(reqs.begin() + i, reqs.begin() + i + take);
+        std::vector<uint64_t> t(tags.begin() + i, tags.begin() + i + take);
+        std::vector<int> slots = engs[e]->admit(r, t);
+        i += take;
         // isolated sources are answered at admission
         std::lock_guard<std::mutex> lk(mu);
-        for (size_t i = 0; i < slots.size(); ++i)
-          if (slots[i] < 0) finish(tags[i], 0, 1.0, 0.0);
+        for (size_t j = 0; j < slots.size(); ++j)
+          if (slots[j] < 0) finish(t[j], 0, 1.0, 0.0);
       }
-      if (eng->active() > 0) {
-        eng->pass();
+      if (active() > 0) {
+        active_sum += active();
         ++passes;
-        active_sum += eng->active();
+        for (auto& e : engs)
+          if (e->active() > 0) e->pass();
         if (++since_collect >= kCollectEvery) {
           since_collect = 0;
-          auto fin = eng->collect(false);
-          while (eng->active() > 0 && eng->compact()) {
+          for (auto& e : engs) {
+            if (e->active() == 0) continue;
+            auto fin = e->collect(false);
+            while (e->active() > 0 && e->compact()) {
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            for (const auto& f : fin) finish(f.tag, f.K, f.C, f.tail_bound);
           }
-          std::lock_guard<std::mutex> lk(mu);
-          for (const auto& f : fin) finish(f.tag, f.K, f.C, f.tail_bound);
         }
       }
     }
@@ -155,13 +179,14 @@ Serve* get_serve(Graph& g) {
   GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = g.cfg.mem_budget ? g.cfg.mem_budget : (size_t)(0.8 * (double)free_b);
   const size_t per_col = ColumnEngine::bytes_per_column(g, GP_F32);
-  int cap = std::min(g.cfg.block_width > 0 ? g.cfg.block_width : 256, 256);  // the engine's widest block
+  const int cap = std::min(g.cfg.block_width > 0 ? g.cfg.block_width : kServeMaxWidth, kServeMaxWidth);
   int width = 8;
   while (width * 2 <= cap && (size_t)(width * 2) * per_col <= budget) width *= 2;
   if ((size_t)width * per_col > budget) throw Error{GP_ENOMEM, "memory budget is below eight query columns"};
   // Columns join at different passes, so they cannot share one 16-bit
   // switch-over: the service stores its blocks in FP32.
-  s->eng.reset(new ColumnEngine(g, width, GP_F32, s->stream));
+  for (int c0 = 0; c0 < width; c0 += kEngineMaxWidth)
+    s->engs.emplace_back(new ColumnEngine(g, std::min(width - c0, kEngineMaxWidth), GP_F32, s->stream));
   s->th = std::thread([p = s.get()] { p->run(); });
   g.serve = s.release();
   return static_cast<Serve*>(g.serve);
@@ -244,7 +269,7 @@ void serve_shutdown(Graph& g) {
     s->cv.notify_all();
   }
   if (s->th.joinable()) s->th.join();
-  s->eng.reset();
+  s->engs.clear();
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
   g.serve = nullptr;

@@ -42,7 +42,7 @@ struct StepArgs {
   int k;               // this pass computes r_{k+1}
   float c_hi, c_lo;    // c_{k+1} as a float pair
   float tail;          // tail(k) (stop test), negative disables the test
-  float tol;
+  float tol;           // l1 tolerance over kCMargin
   int cheb;            // 1: Chebyshev recurrence, 0: power step r_{k+1} = P r_k
 };
 
@@ -258,7 +258,8 @@ __device__ __forceinline__ void finish_chunk(Ctx& c, const TileInfo& t, const in
 }
 
 // The stop test at the top of pass k: stop once tail(k) * max_{l<=k} ||r_l||_1
-// <= tol (Theorem 1 with the measured C).  Thread-local; the caller shares it.
+// <= tol, where tol is the caller's l1 tolerance over kCMargin (Theorem 1 with
+// Assumption 1's C estimated on the fly).  Thread-local; the caller shares it.
 __device__ __forceinline__ int pass_stopped(const StepArgs& a) {
   if (a.tail < 0.f) return 0;
   float C = 0.f;

@@ -29,6 +29,7 @@ def main():
     p.add_argument("--width", type=int, default=0, help="block width (0: from the query count)")
     p.add_argument("--tol", type=float, default=None, help="l1 tolerance (default 1e-4 batch, 1e-6 single)")
     p.add_argument("--reps", type=int, default=2)
+    p.add_argument("--k-fixed", type=int, default=0, help="batch: every query runs exactly this K (0: stop rule)")
     args = p.parse_args()
 
     import torch
@@ -44,7 +45,8 @@ def main():
         dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=storage,
                                 block_width=args.width)
         ys = [torch.empty(g.n, dtype=torch.float64, device="cuda") for _ in queries]
-        reqs = [gp.make_request(fn, s, a, tol, ys[i]) for i, (fn, s, a) in enumerate(queries)]
+        kw = dict(k_rule=gp.GP_K_FIXED, k_fixed=args.k_fixed) if args.k_fixed > 0 else {}
+        reqs = [gp.make_request(fn, s, a, tol, ys[i], **kw) for i, (fn, s, a) in enumerate(queries)]
         for _ in range(args.reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()

@@ -22,6 +22,8 @@ import oracle as O
 ORACLE_DIR = os.path.dirname(os.path.abspath(O.__file__))
 
 MUTANTS = {
+    # the l1 stop rule with the running maximum alone (no margin on C)
+    "no_c_margin": ("tail[k] * OR_C_MARGIN * C > tol", "tail[k] * C > tol"),
     # alpha-walk: stops with probability 1 - alpha
     "walk_stop_flipped": ("if (u < alpha || d == 0) return v;", "if (u >= alpha || d == 0) return v;"),
     # Algorithm 5: the residual with the wrong sign of the (1 - alpha) P term
@@ -82,6 +84,11 @@ def _pins_hold(M):
     want = np.array([np.sum(fl * np.cos(2 * np.pi * j * (u - 5) / n)) / n for u in range(n)])
     ok &= bool(np.max(np.abs(M.chebypower(cyc, 5, "ppr", 0.2, 80) - want)) < 1e-12)
     ok &= bool(np.max(np.abs(M.chebypower(g, s, "ppr", 0.2, 80) - M.dense_ppr(g, s, 0.2))) < 1e-12)
+    # the stop rule's margin (a query whose ||r_k||_1 grows after the running-max stop)
+    gm = gg.rmat(14, 16, seed=2)
+    sm = int(gg.sources(gm, 320, 23)[177])
+    ym, Km, _ = M.chebypower_tol(gm, sm, "hkpr", 3.0, 1e-6)
+    ok &= Km == 12 and bool(np.abs(ym - M.chebypower(gm, sm, "hkpr", 3.0, 150)).sum() <= 1e-6)
     # ChebyPush: the worked example (Section 4) and Theorem 3's degree-normalised bound
     c3e = np.array([0.0, 0.0, 0.0, 1.0])
     _, r3 = M.chebypush(star, 1, "ppr", 0.2, 3, eps=np.full(4, 1 / 3), coeffs=c3e, rule=1, return_r=True)

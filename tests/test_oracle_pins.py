@@ -244,6 +244,23 @@ def test_stopping_rule_meets_l1():
                 assert np.max(np.abs(yK - y)) < 1e-15
 
 
+def test_stopping_rule_margin_covers_growing_norms():
+    # On R-MAT 14 the norms ||r_k||_1 of this HKPR t = 3 query still grow after
+    # the running-maximum rule would stop (K = 11, truncation 1.07e-6 > 1e-6):
+    # the margin of 2 on the measured C keeps the truncation within tol.
+    g = gg.rmat(14, 16, seed=2)
+    s = int(gg.sources(g, 320, 23)[177])
+    ystar = O.chebypower(g, s, "hkpr", 3.0, 150)
+    y11 = O.chebypower(g, s, "hkpr", 3.0, 11)
+    assert O.errors(g, ystar, y11)["l1"] > 1e-6  # where the rule without margin stops
+    y, K, norms = O.chebypower_tol(g, s, "hkpr", 3.0, 1e-6)
+    assert K == 12
+    c = O.cheb_coeffs("hkpr", 3.0, 200)
+    assert np.abs(c[12:]).sum() * norms.max() > 1e-6 / 2  # K = 11 fails the margin
+    assert np.abs(c[13:]).sum() * norms.max() <= 1e-6 / 2
+    assert O.errors(g, ystar, y)["l1"] <= 1e-6
+
+
 def test_chebypower_norms_and_K1():
     g = gg.erdos_renyi(200, 800, 2)
     s = int(gg.sources(g, 1, 1)[0])
