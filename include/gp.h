@@ -72,11 +72,13 @@ typedef struct {
                               GP_F32, GP_BF16 or GP_F16 (16-bit ones with the FP32
                               warm-up schedule); single queries always use GP_F32 */
   int32_t block_width;     /* B, columns per batched SpMM pass; 0 = autotune */
-  int32_t autotune;        /* 1: gp_batch with block_width 0 uses the width gp_autotune picks */
+  int32_t autotune;        /* 1: gp_batch uses gp_autotune's width (block_width 0) and degree
+                              threshold (t_heavy 0) */
   int32_t k_max;           /* hard cap on K (default 96) */
   int32_t validate_symmetry; /* 1 (default): check that every (u,v) has (v,u) */
-  int32_t t_heavy;         /* rows with degree >= t_heavy are summed in pieces by several warps
-                              (0: only rows too long for one whole-row task, > 508 entries) */
+  int32_t t_heavy;         /* rows with degree >= t_heavy are summed in pieces by several warps,
+                              single and batched queries (0: only rows too long for one
+                              whole-row task, > 508 entries, or the tuned threshold) */
   int32_t row_ptr_64;      /* 1: keep 64-bit row offsets even when nnz fits 32 bits (default 0) */
   int32_t precise_rows;    /* single queries on graphs with at most this many non-isolated nodes
                               keep T_k as float pairs (~48 bits) instead of FP32: FP32 rounding
@@ -247,21 +249,25 @@ gp_status gp_ppr_bidirectional(gp_graph* g, int32_t source, double alpha, double
                                uint64_t seed, gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info);
 
 /*
- * Autotuner for the batched form (the block width B; the paper has no
- * counterpart).  Times fused SpMM passes of the column engine on this graph at
- * each candidate width (powers of two in [8, 256]; widths == NULL means 8,
- * 16, 32, 64, 128, 256) with CUDA events on the graph's stream, for `storage` (16-bit
- * storage: 0.45 of an FP32 warm-up pass plus 0.55 of a 16-bit pass), and
- * returns the width with the least device time per column and pass in
- * *best_width, and that time in microseconds in *us_per_column_pass
- * (nullable).  The default-candidate result is cached per graph structure (n,
- * nnz and degree sequence), storage and device; gp_batch uses it when
- * cfg.block_width is 0 and cfg.autotune is 1.  Allocates and frees one column
- * block per candidate; candidates that need more than half of the free device
- * memory are skipped (GP_EINVAL if none fits).
+ * Autotuner for the batched form (the block width B and the degree threshold
+ * of the chunked rows; the paper has no counterpart).  Times fused SpMM passes
+ * of the column engine on this graph with CUDA events on the graph's stream,
+ * for `storage` (16-bit storage: 0.45 of an FP32 warm-up pass plus 0.55 of a
+ * 16-bit pass): first at each candidate width (powers of two in [8, 256];
+ * widths == NULL means 8, 16, 32, 64, 128, 256) with rows of more than 508
+ * entries chunked, then at the best width with the rows of degree >= 65, 129
+ * or 257 chunked (summed in pieces by several warps).  Returns the width with
+ * the least device time per column and pass in *best_width, the degree
+ * threshold in *best_t_heavy (nullable; the value cfg.t_heavy would take), and
+ * that time in microseconds in *us_per_column_pass (nullable).  The
+ * default-candidate result is cached per graph structure (n, nnz and degree
+ * sequence), storage and device; with cfg.autotune = 1, gp_batch uses its
+ * width when cfg.block_width is 0 and its threshold when cfg.t_heavy is 0.
+ * Allocates and frees one column block per trial; candidates that need more
+ * than half of the free device memory are skipped (GP_EINVAL if none fits).
  */
 gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int32_t nwidths, int32_t* best_width,
-                      double* us_per_column_pass);
+                      int32_t* best_t_heavy, double* us_per_column_pass);
 
 /*
  * Continuous-batching service.  gp_submit queues a request and returns a

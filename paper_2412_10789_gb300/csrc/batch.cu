@@ -1178,10 +1178,12 @@ void launch_stage(const SpmmArgs& a, int stage, cudaStream_t st) {
 
 // ------------------------------------------------------------------ engine
 
-ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st)
+ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long)
     : g_(g), B_(B), bw_(B), storage_(storage), st_(st) {
   if (B < 8 || B > 256 || (B & (B - 1)))
     throw Error{GP_EINVAL, "block width must be a power of two in [8, 256]"};
+  if (t_long <= 0) t_long = g.cfg.t_heavy > 0 ? g.cfg.t_heavy - 1 : kBTileCap;
+  t_long_ = std::max(1, std::min(t_long, kBTileCap));
   if (storage != GP_F32 && storage != GP_BF16 && storage != GP_F16)
     throw Error{GP_EINVAL, "storage must be GP_F32, GP_BF16 or GP_F16"};
   kcap_ = std::min(g.cfg.k_max, kMaxColK - 2);
@@ -1201,14 +1203,16 @@ ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st)
     norm_ = (float*)A.get(sizeof(float) * B);
     scratch_ = (int*)A.get(sizeof(int) * 4 * B + sizeof(int64_t) * B + sizeof(float) * 2 * B + 16);
     outs_ = A.get(sizeof(void*) * B);
-    // tiles of the pass: chunks of the long rows, then runs of equal-degree rows
+    // tiles of the pass: chunks of the long rows (more than t_long_ entries;
+    // the relabelled rows are in descending degree, so they come first), then
+    // runs of equal-degree rows
     const std::vector<int64_t>& rp = g.h_rp_relabelled;
     const int EG = 32 / (B / 8);
     std::vector<int4> tiles;
     std::vector<int> poff(1, 0);
     std::vector<int64_t> ldeg;
     int64_t row = 0;
-    while (row < g.n_active && rp[row + 1] - rp[row] > kBTileCap) {
+    while (row < g.n_active && rp[row + 1] - rp[row] > t_long_) {
       const int64_t deg = rp[row + 1] - rp[row];
       const int64_t np = (deg + kBTileCap - 1) / kBTileCap;
       if (np > 0x7fff) throw Error{GP_EINVAL, "a row has too many entries for the batched schedule"};
@@ -1608,17 +1612,25 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
     // the next power of two that holds the requests, within [8, 256]; with
     // cfg.autotune, no wider than the tuned width of this graph and storage
     B = std::min(256, std::max(8, (int)(1u << (32 - __builtin_clz((unsigned)std::max(count, 8) - 1)))));
-    if (g.cfg.autotune) B = std::min(B, tuned_width(g, g.cfg.storage, {}, nullptr));
+  }
+  // cfg.autotune: the tuned width (an upper bound when block_width is 0) and,
+  // unless cfg.t_heavy sets it, the tuned chunk threshold
+  int t_long = 0;
+  if (g.cfg.autotune) {
+    const TunedBlock tb = tune_block(g, g.cfg.storage, {});
+    if (g.cfg.block_width <= 0) B = std::min(B, tb.B);
+    if (g.cfg.t_heavy <= 0) t_long = tb.t_long;
   }
   BatchCache* bc = static_cast<BatchCache*>(g.batch);
   if (!bc) {
     bc = new BatchCache();
     g.batch = bc;
   }
-  if (!bc->eng || bc->B != B || bc->storage != g.cfg.storage) {
+  if (!bc->eng || bc->B != B || bc->storage != g.cfg.storage || bc->t_long != t_long) {
     bc->eng.reset();
-    bc->eng.reset(new ColumnEngine(g, B, g.cfg.storage, g.stream));
+    bc->eng.reset(new ColumnEngine(g, B, g.cfg.storage, g.stream, t_long));
     bc->B = B;
+    bc->t_long = t_long;
     bc->storage = g.cfg.storage;
   }
   ColumnEngine& eng = *bc->eng;
@@ -1693,6 +1705,7 @@ void run_clenshaw(Graph& g, int count, const gp_request* reqs, gp_query_info* in
     bc->eng.reset();
     bc->eng.reset(new ColumnEngine(g, B, g.cfg.storage, g.stream));
     bc->B = B;
+    bc->t_long = 0;
     bc->storage = g.cfg.storage;
   }
   ColumnEngine& eng = *bc->eng;
@@ -1765,6 +1778,7 @@ void run_propagate(Graph& g, int function, double param, double a, int F, const 
         bc->eng.reset();
         bc->eng.reset(new ColumnEngine(g, B, g.cfg.storage, st));
         bc->B = B;
+        bc->t_long = 0;
         bc->storage = g.cfg.storage;
       }
       auto t0 = std::chrono::steady_clock::now();
@@ -1811,7 +1825,7 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, double>> g_tune;  // width, us per column-pass
+std::map<TuneKey, TunedBlock> g_tune;
 
 // Mean device time (ms) of `reps` passes of one engine at a forced storage stage.
 double time_passes(ColumnEngine& eng, int stage, int reps, cudaStream_t st) {
@@ -1831,12 +1845,14 @@ double time_passes(ColumnEngine& eng, int stage, int reps, cudaStream_t st) {
 }
 }  // namespace
 
-// Time the column engine at each candidate width on this graph (every column
-// a fixed-K query from a distinct non-isolated node, so nothing retires), and
-// return the width with the least device time per column and pass.  With
-// 16-bit storage a block spends about its first half in the FP32 warm-up, so
-// the cost is 0.45 of an FP32 pass plus 0.55 of a 16-bit one.
-int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_out) {
+// Time the column engine on this graph (every column a fixed-K query from a
+// distinct non-isolated node, so nothing retires) at each candidate width,
+// then, at the best width, at each candidate chunk threshold (rows with more
+// entries than the threshold are summed as chunk tiles by several warps); keep
+// the pair with the least device time per column and pass.  With 16-bit
+// storage a block spends about its first half in the FP32 warm-up, so the cost
+// is 0.45 of an FP32 pass plus 0.55 of a 16-bit one.
+TunedBlock tune_block(Graph& g, gp_dtype storage, std::vector<int> widths) {
   int dev = 0;
   GP_CUDA_TRY(cudaGetDevice(&dev));
   const TuneKey key{g.digest, (int)storage, dev};
@@ -1844,24 +1860,21 @@ int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_
   if (!custom) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) {
-      if (us_out) *us_out = it->second.second;
-      return it->second.first;
-    }
+    if (it != g_tune.end()) return it->second;
     widths = {8, 16, 32, 64, 128, 256};
   }
+  for (int B : widths)
+    GP_REQUIRE(B >= 8 && B <= 256 && (B & (B - 1)) == 0, "widths must be powers of two in [8, 256]");
   std::vector<int32_t> srcs;
   for (int64_t u = 0; u < g.n && (int)srcs.size() < 256; ++u)
     if (g.h_deg[u] > 0) srcs.push_back((int32_t)u);
   GP_REQUIRE(!srcs.empty(), "the graph has no edges");
-  int best = 0;
-  double best_us = 0.0;
-  for (int B : widths) {
-    GP_REQUIRE(B >= 8 && B <= 256 && (B & (B - 1)) == 0, "widths must be powers of two in [8, 256]");
+  // device time per column and pass of one (width, threshold); < 0 if it does not fit
+  auto trial = [&](int B, int t_long) -> double {
     size_t free_b = 0, total_b = 0;
     GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    if ((size_t)B * ColumnEngine::bytes_per_column(g, storage) > free_b / 2) continue;
-    ColumnEngine eng(g, B, storage, g.stream);
+    if ((size_t)B * ColumnEngine::bytes_per_column(g, storage) > free_b / 2) return -1.0;
+    ColumnEngine eng(g, B, storage, g.stream, t_long);
     std::vector<gp_request> reqs(B);
     std::vector<uint64_t> tags(B);
     for (int j = 0; j < B; ++j) {
@@ -1882,18 +1895,22 @@ int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_
     eng.admit(reqs, tags);
     const double t32 = time_passes(eng, 0, 2, g.stream);
     const double ms = storage == GP_F32 ? t32 : 0.45 * t32 + 0.55 * time_passes(eng, 3, 2, g.stream);
-    const double us = 1000.0 * ms / B;
-    if (best == 0 || us < best_us) {
-      best = B;
-      best_us = us;
-    }
+    return 1000.0 * ms / B;
+  };
+  TunedBlock best{0, kBTileCap, 0.0};
+  for (int B : widths) {
+    const double us = trial(B, kBTileCap);
+    if (us >= 0.0 && (best.B == 0 || us < best.us)) best = TunedBlock{B, kBTileCap, us};
   }
-  GP_REQUIRE(best > 0, "no candidate width fits in device memory");
+  GP_REQUIRE(best.B > 0, "no candidate width fits in device memory");
+  for (int t : {64, 128, 256}) {
+    const double us = trial(best.B, t);
+    if (us >= 0.0 && us < best.us) best = TunedBlock{best.B, t, us};
+  }
   if (!custom) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = {best, best_us};
+    g_tune[key] = best;
   }
-  if (us_out) *us_out = best_us;
   return best;
 }
 

@@ -50,7 +50,10 @@ class ColumnEngine {
     std::chrono::steady_clock::time_point t_admit;
   };
 
-  ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st);
+  // t_long: rows with more entries become chunk tiles (at most kBTileCap;
+  // 0: from cfg.t_heavy, else kBTileCap).
+  ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long = 0);
+  int t_long() const { return t_long_; }
   ~ColumnEngine();
   ColumnEngine(const ColumnEngine&) = delete;
   ColumnEngine& operator=(const ColumnEngine&) = delete;
@@ -105,6 +108,7 @@ class ColumnEngine {
 
   Graph& g_;
   int B_;
+  int t_long_ = 0;  // rows with more entries are chunk tiles
   int bw_ = 0;  // columns of each pass (a prefix of B_)
   gp_dtype storage_;
   cudaStream_t st_;
@@ -151,6 +155,7 @@ class ColumnEngine {
 struct BatchCache {
   std::unique_ptr<ColumnEngine> eng;
   int B = 0;
+  int t_long = 0;
   gp_dtype storage = GP_F32;
 };
 

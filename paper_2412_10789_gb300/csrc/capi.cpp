@@ -185,7 +185,7 @@ extern "C" gp_status gp_ppr_bidirectional(gp_graph* gh, int32_t source, double a
 }
 
 extern "C" gp_status gp_autotune(gp_graph* gh, gp_dtype storage, const int32_t* widths, int32_t nwidths,
-                                  int32_t* best_width, double* us_per_column_pass) {
+                                  int32_t* best_width, int32_t* best_t_heavy, double* us_per_column_pass) {
   return guard([&] {
     Graph* g = as_graph(gh);
     GP_REQUIRE(best_width, "best_width is NULL");
@@ -193,10 +193,10 @@ extern "C" gp_status gp_autotune(gp_graph* gh, gp_dtype storage, const int32_t* 
     GP_REQUIRE(nwidths >= 0 && (nwidths == 0 || widths), "widths is NULL");
     std::vector<int> w(widths, widths + nwidths);
     std::lock_guard<std::recursive_mutex> lk(g->mu);
-    double us = 0.0;
-    const int b = tuned_width(*g, storage, w, &us);
-    *best_width = b;
-    if (us_per_column_pass) *us_per_column_pass = us;
+    const TunedBlock tb = tune_block(*g, storage, w);
+    *best_width = tb.B;
+    if (best_t_heavy) *best_t_heavy = tb.t_long + 1;
+    if (us_per_column_pass) *us_per_column_pass = tb.us;
   });
 }
 

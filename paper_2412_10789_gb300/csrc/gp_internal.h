@@ -202,7 +202,14 @@ void run_bidirectional(Graph& g, int32_t source, double alpha, double eps_r, dou
                        gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info);
 // Block width with the least device time per column and pass on this graph
 // (cached per graph digest, storage and device unless widths are given).
-int tuned_width(Graph& g, gp_dtype storage, std::vector<int> widths, double* us_per_column_pass);
+// The batched form's tuned block: width B, chunk threshold t_long (rows with
+// more entries are chunk tiles) and the device time per column and pass.
+struct TunedBlock {
+  int B;
+  int t_long;
+  double us;
+};
+TunedBlock tune_block(Graph& g, gp_dtype storage, std::vector<int> widths);
 void free_batch_work(Graph& g);
 uint64_t serve_submit(Graph& g, const gp_request& req);
 gp_status serve_poll(Graph& g, uint64_t ticket, gp_query_info* info);

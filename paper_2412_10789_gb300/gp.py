@@ -129,7 +129,7 @@ def load_library():
             "gp_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                               ctypes.POINTER(dbl)]),
             "gp_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(i32), i32, ctypes.POINTER(i32),
-                                           ctypes.POINTER(dbl)]),
+                                           ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
             "gp_launch_count": (u64, []),
             "gp_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
             "gp_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(dbl)]),
@@ -419,14 +419,15 @@ def gp_profile_enable(g: Graph, on: bool = True):
 
 
 def gp_autotune(g: Graph, storage=None, widths=None):
-    """Block width with the least device time per column and pass on this graph."""
+    """Block width and chunked-row degree threshold with the least device time
+    per column and pass on this graph."""
     lib = load_library()
     st = g.storage if storage is None else storage
     arr = (ctypes.c_int32 * len(widths))(*widths) if widths else None
-    best, us = ctypes.c_int32(), ctypes.c_double()
+    best, th, us = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(lib.gp_autotune(g.handle, int(st), arr, len(widths) if widths else 0, ctypes.byref(best),
-                           ctypes.byref(us)))
-    return {"width": best.value, "us_per_column_pass": us.value}
+                           ctypes.byref(th), ctypes.byref(us)))
+    return {"width": best.value, "t_heavy": th.value, "us_per_column_pass": us.value}
 
 
 def gp_profile_read(g: Graph):

@@ -39,6 +39,33 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def _param_counts():
+    """Number of parameters of every function declared in include/*.h."""
+    counts = {}
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", h)).read(), flags=re.S)
+        for m in re.finditer(r"\b(gp_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
+            args = m.group(2).strip()
+            if "(" in args:  # a function-pointer member, not a declaration
+                continue
+            counts[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return counts
+
+
+def test_binding_signatures_match_the_header(lib):
+    counts = _param_counts()
+    checked = 0
+    for name, n in counts.items():
+        f = getattr(lib, name)
+        if f.argtypes is None:
+            continue
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+        checked += 1
+    assert checked >= 20
+
+
 def test_status_strings_and_defaults(lib):
     from paper_2412_10789_gb300 import gp
     assert gp.gp_status_string(gp.GP_OK) == "GP_OK"

@@ -179,7 +179,8 @@ def test_int64_row_offsets(gp):
                 for i, v in enumerate(gg.sources(g, 3, 43))]
         gp.gp_batch(dg, reqs)
         for i, v in enumerate(gg.sources(g, 3, 43)):
-            e = O.errors(g, O.chebypower(g, int(v), "hkpr", 5.0, 15), ys[i].cpu().numpy())
-            assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7, e
+            want = O.chebypower(g, int(v), "hkpr", 5.0, 15)
+            e = O.errors(g, want, ys[i].cpu().numpy())
+            assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7 + 15 * 2.0 ** -24 * np.abs(want).max(), e
     finally:
         dg.close()
