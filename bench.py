@@ -66,7 +66,7 @@ def parse():
                    help="rmat22: the headline single-source workload; the others time the batched and "
                         "served forms on the larger graphs")
     p.add_argument("--requests", type=int, default=10000, help="chunglu24_serve: requests per load level")
-    p.add_argument("--serve-width", type=int, default=512,
+    p.add_argument("--serve-width", type=int, default=256,
                    help="chunglu24_serve: query slots of the service block (a power of two, <= 512)")
     p.add_argument("--loads", default="0.5,0.8,0.95", help="chunglu24_serve: offered load levels")
     return p.parse_args()

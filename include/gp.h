@@ -277,9 +277,9 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
  * one step per fused SpMM pass, retires a column when its stop rule fires
  * (writing y_out before the ticket completes) and refills the slot.  The
  * block has as many slots as the memory budget allows (cfg.mem_budget, default
- * 80% of the free device memory), at most cfg.block_width (0: 512), a power of
- * two; a block wider than 256 columns runs as 256-column halves, each with its
- * own pass.  The request's y_out must stay valid until gp_poll reports
+ * 80% of the free device memory), at most cfg.block_width (0: 256; 512 at most),
+ * a power of two; a block wider than 256 columns runs as 256-column halves,
+ * each with its own pass.  The request's y_out must stay valid until gp_poll reports
  * completion.
  * gp_poll returns GP_OK (and fills info) once the ticket is done, GP_EAGAIN
  * before that, GP_ENOTFOUND for an unknown or already-collected ticket.

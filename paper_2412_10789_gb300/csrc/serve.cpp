@@ -2,19 +2,21 @@
 //
 // One service thread per graph owns the column engines (batch.h) of its block
 // on its own stream.  The block's width (columns = query slots) is what the
-// memory budget allows (cfg.mem_budget, default 80% of the free device memory,
-// at ColumnEngine::bytes_per_column each, capped by cfg.block_width or 512),
-// so a free column is also free memory for one more query.  A warp spans at
-// most 256 FP32 columns of a row, so a 512-column block is two 256-column
-// engines, each advanced by its own fused pass.  Each iteration admits queued
-// requests into free columns (first engine first), runs one fused pass over
-// the active columns of each engine that has any (the per-column stop rule
-// runs on the device in the pass's control kernel), and every few passes
-// collects the retired columns: their y is written to the request's y_out,
-// the ticket completes, and the column is free for the next request.  Passes cover only the prefix of columns that holds
-// the busy ones, and the busy columns are moved to the front when at most
-// half of that prefix is busy, so a lightly loaded service runs narrow passes.  Requests therefore join and leave the running block
-// while the others keep going; their work shares every pass.
+// memory budget allows (cfg.mem_budget, default 80% of the free device
+// memory, at ColumnEngine::bytes_per_column each), capped by cfg.block_width
+// (256 by default, 512 at most), so a free column is also free memory for one
+// more query.  A warp spans at most 256 FP32 columns of a row, so a
+// 512-column block is two 256-column engines, each advanced by its own fused
+// pass.  Each iteration admits queued requests into free columns (first
+// engine first), runs one fused pass over the active columns of each engine
+// that has any (the per-column stop rule runs on the device in the pass's
+// control kernel), and every few passes collects the retired columns: their y
+// is written to the request's y_out, the ticket completes, and the column is
+// free for the next request.  Passes cover only the prefix of columns that
+// holds the busy ones, and the busy columns are moved to the front when at
+// most half of that prefix is busy, so a lightly loaded service runs narrow
+// passes.  Requests therefore join and leave the running block while the
+// others keep going; their work shares every pass.
 #include <algorithm>
 #include <condition_variable>
 #include <cstring>
@@ -31,8 +33,9 @@ namespace gp {
 namespace {
 
 constexpr size_t kQueueCap = 1 << 20;
-constexpr int kServeMaxWidth = 512;   // query slots of the service's block
-constexpr int kEngineMaxWidth = 256;  // columns of one engine
+constexpr int kServeMaxWidth = 512;      // query slots of the service's block, at most
+constexpr int kServeDefaultWidth = 256;  // ... when cfg.block_width is 0
+constexpr int kEngineMaxWidth = 256;     // columns of one engine
 constexpr int kCollectEvery = 2;
 
 struct Ticket {
@@ -179,7 +182,9 @@ Serve* get_serve(Graph& g) {
   GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = g.cfg.mem_budget ? g.cfg.mem_budget : (size_t)(0.8 * (double)free_b);
   const size_t per_col = ColumnEngine::bytes_per_column(g, GP_F32);
-  const int cap = std::min(g.cfg.block_width > 0 ? g.cfg.block_width : kServeMaxWidth, kServeMaxWidth);
+  // 256 slots already keep the GPU busy on large graphs; more slots add
+  // concurrency, not throughput, and lengthen every pass (latency under load)
+  const int cap = std::min(g.cfg.block_width > 0 ? g.cfg.block_width : kServeDefaultWidth, kServeMaxWidth);
   int width = 8;
   while (width * 2 <= cap && (size_t)(width * 2) * per_col <= budget) width *= 2;
   if ((size_t)width * per_col > budget) throw Error{GP_ENOMEM, "memory budget is below eight query columns"};

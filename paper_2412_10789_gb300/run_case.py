@@ -42,8 +42,8 @@ def main():
     storage = {"fp32": gp.GP_F32, "bf16": gp.GP_BF16, "fp16": gp.GP_F16}[args.storage]
     if args.form == "batch":
         tol = 1e-4 if args.tol is None else args.tol
-        dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, storage=storage,
-                                block_width=args.width)
+        rp = g.row_ptr if g.nnz > 2**31 - 1 else g.row_ptr32()
+        dg = gp.gp_graph_create(g.n, rp, g.col_idx, g.degree, storage=storage, block_width=args.width)
         ys = [torch.empty(g.n, dtype=torch.float64, device="cuda") for _ in queries]
         kw = dict(k_rule=gp.GP_K_FIXED, k_fixed=args.k_fixed) if args.k_fixed > 0 else {}
         reqs = [gp.make_request(fn, s, a, tol, ys[i], **kw) for i, (fn, s, a) in enumerate(queries)]
