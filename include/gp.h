@@ -224,7 +224,10 @@ gp_status gp_propagate(gp_graph* g, int32_t function, double param, double a, in
  * Theorem 3 bounds the degree-normalised error: max_u |y(u) - y^(u)| / d_u <
  * eps_a once the truncation is below eps_a / 2; K = 0 picks the smallest K
  * with sum_{l>=K} |c_l| <= eps_a / 2 (1 <= K <= 1024 otherwise).  The vectors
- * are FP64 on the device.  Output as in gp_ppr (out_dtype GP_F64 or GP_F32,
+ * are FP64 on the device; the graph's first push query allocates them (three
+ * n-vectors and the frontier, about 24 n + 16 (n + nnz / 2048) bytes, plus n
+ * doubles of staging for host outputs) and keeps them until
+ * gp_graph_destroy, so later push queries allocate nothing.  Output as in gp_ppr (out_dtype GP_F64 or GP_F32,
  * device or host).  info (nullable): K; tail_bound = sum_{l>=K} |c_l|;
  * max_r_l1 = the number of push items (frontier rows, long rows counted per
  * 2048 entries) over all iterations.

@@ -133,6 +133,20 @@ struct Schedule {
 
 // ----------------------------------------------------------------- graph
 
+// ChebyPush / Algorithm 5 work vectors (push.cu), allocated at a graph's first
+// push query and kept until the graph is destroyed, so a query allocates
+// nothing.
+struct PushWork {
+  double* ra = nullptr;  // r_cur / r_new pair, n each
+  double* rb = nullptr;
+  double* y = nullptr;   // n
+  int2* fr = nullptr;    // frontier items {row, chunk}
+  double* fval = nullptr;
+  int* counts = nullptr;                  // frontier items per iteration (1025)
+  unsigned long long* walks = nullptr;    // walks taken (Algorithm 5)
+  void* stage = nullptr;                  // host-output staging, n doubles (on demand)
+};
+
 struct QueryWork {
   float* qa = nullptr;      // Q = D^-1 r, one buffer of the ping-pong pair
   float* qb = nullptr;      // the other
@@ -162,6 +176,7 @@ struct Graph {
   bool own_stream = false;
   std::recursive_mutex mu;
   QueryWork qw;
+  PushWork pw;
   // kernel timing (gp_profile_*)
   bool profiling = false;
   double prof_ms = 0.0;
@@ -194,6 +209,7 @@ void run_batch(Graph& g, int count, const gp_request* reqs, gp_query_info* infos
 void run_clenshaw(Graph& g, int count, const gp_request* reqs, gp_query_info* infos);
 void run_propagate(Graph& g, int function, double param, double a, int F, const float* X, float* Z, int on_device,
                    double tol, gp_query_info* infos);
+void free_push_work(Graph& g);
 // push.cu: ChebyPush (Algorithm 4) for one source.
 void run_chebypush(Graph& g, int function, int32_t source, double param, double eps_a, int K, gp_dtype out_dtype,
                    void* y_out, int y_on_device, gp_query_info* info);

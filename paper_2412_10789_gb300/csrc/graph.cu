@@ -286,6 +286,7 @@ void destroy_graph(Graph* g) {
   serve_shutdown(*g);
   free_batch_work(*g);
   free_query_work(*g);
+  free_push_work(*g);
   free_schedule(*g);
   g->alloc.put(g->rp);
   g->alloc.put(g->ci);

@@ -18,7 +18,8 @@
 // their order changes only the rounding of r_new; the vectors are FP64 so that
 // the threshold decisions follow the FP64 reference.  Scanning every row
 // costs 8 bytes per row and iteration; the pushes cost what the frontier
-// holds.
+// holds.  The work vectors are allocated at the graph's first push query and
+// kept with the graph (PushWork), so a query allocates nothing.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -177,6 +178,38 @@ int sms() {
   return s > 0 ? s : 1;
 }
 
+constexpr int kPushKCap = 1024;  // longest iteration count of a push query
+
+// The graph's push work vectors (allocated once); the host-output staging
+// buffer only when a query writes to host memory.
+PushWork& push_work(Graph& g, bool need_stage) {
+  PushWork& w = g.pw;
+  Allocator& A = g.alloc;
+  const int64_t n = std::max<int64_t>(g.n, 1), na = std::max<int64_t>(g.n_active, 1);
+  if (!w.ra) {
+    // frontier: at most one item per kPushChunk entries plus one per row
+    const int64_t cap = na + g.nnz / kPushChunk + 1;
+    PushWork t;
+    try {
+      t.ra = (double*)A.get(sizeof(double) * n);
+      t.rb = (double*)A.get(sizeof(double) * n);
+      t.y = (double*)A.get(sizeof(double) * n);
+      t.fr = (int2*)A.get(sizeof(int2) * cap);
+      t.fval = (double*)A.get(sizeof(double) * cap);
+      t.counts = (int*)A.get(sizeof(int) * (kPushKCap + 1));
+      t.walks = (unsigned long long*)A.get(sizeof(unsigned long long));
+    } catch (...) {
+      for (void* p : {(void*)t.ra, (void*)t.rb, (void*)t.y, (void*)t.fr, (void*)t.fval, (void*)t.counts,
+                      (void*)t.walks})
+        A.put(p);
+      throw;
+    }
+    w = t;
+  }
+  if (need_stage && !w.stage) w.stage = A.get(sizeof(double) * n);
+  return w;
+}
+
 template <typename RP>
 void run_push_rp(Graph& g, int64_t s, const std::vector<double>& c, int K, double eps_a, double* rcur, double* rnew,
                  double* y, int2* fr, double* fval, int* counts, int64_t* pushed) {
@@ -243,42 +276,31 @@ void run_chebypush(Graph& g, int function, int32_t source, double param, double 
                                 y_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
     GP_CUDA_TRY(cudaStreamSynchronize(st));
   } else {
-    Allocator& A = g.alloc;
-    const int64_t n = std::max<int64_t>(g.n, 1), na = std::max<int64_t>(g.n_active, 1);
-    double* ra = (double*)A.get(sizeof(double) * n);
-    double* rb = (double*)A.get(sizeof(double) * n);
-    double* y = (double*)A.get(sizeof(double) * n);
-    // frontier: at most one item per kPushChunk entries plus one per row
-    const int64_t cap = na + g.nnz / kPushChunk + 1;
-    int2* fr = (int2*)A.get(sizeof(int2) * cap);
-    double* fval = (double*)A.get(sizeof(double) * cap);
-    int* counts = (int*)A.get(sizeof(int) * (K + 1));
-    void* stage = y_on_device ? nullptr : A.get(esz * n);
+    PushWork& w = push_work(g, !y_on_device);
+    const int64_t n = std::max<int64_t>(g.n, 1);
     try {
-      GP_CUDA_TRY(cudaMemsetAsync(ra, 0, sizeof(double) * n, st));
-      GP_CUDA_TRY(cudaMemsetAsync(rb, 0, sizeof(double) * n, st));
-      GP_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
-      GP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
+      GP_CUDA_TRY(cudaMemsetAsync(w.ra, 0, sizeof(double) * n, st));
+      GP_CUDA_TRY(cudaMemsetAsync(w.rb, 0, sizeof(double) * n, st));
+      GP_CUDA_TRY(cudaMemsetAsync(w.y, 0, sizeof(double) * n, st));
+      GP_CUDA_TRY(cudaMemsetAsync(w.counts, 0, sizeof(int) * (K + 1), st));
       const int64_t s = g.h_newid[source];
       if (g.rp64)
-        run_push_rp<int64_t>(g, s, c, K, eps_a, ra, rb, y, fr, fval, counts, &pushed);
+        run_push_rp<int64_t>(g, s, c, K, eps_a, w.ra, w.rb, w.y, w.fr, w.fval, w.counts, &pushed);
       else
-        run_push_rp<int32_t>(g, s, c, K, eps_a, ra, rb, y, fr, fval, counts, &pushed);
-      void* dst = y_on_device ? y_out : stage;
+        run_push_rp<int32_t>(g, s, c, K, eps_a, w.ra, w.rb, w.y, w.fr, w.fval, w.counts, &pushed);
+      void* dst = y_on_device ? y_out : w.stage;
       const int grid = sms() * 4;
       if (out_dtype == GP_F64)
-        push_output_kernel<double><<<grid, 256, 0, st>>>(g.n, g.newid, y, (double*)dst);
+        push_output_kernel<double><<<grid, 256, 0, st>>>(g.n, g.newid, w.y, (double*)dst);
       else
-        push_output_kernel<float><<<grid, 256, 0, st>>>(g.n, g.newid, y, (float*)dst);
+        push_output_kernel<float><<<grid, 256, 0, st>>>(g.n, g.newid, w.y, (float*)dst);
       GP_LAUNCHED();
-      if (!y_on_device) GP_CUDA_TRY(cudaMemcpyAsync(y_out, stage, esz * g.n, cudaMemcpyDeviceToHost, st));
+      if (!y_on_device) GP_CUDA_TRY(cudaMemcpyAsync(y_out, w.stage, esz * g.n, cudaMemcpyDeviceToHost, st));
       GP_CUDA_TRY(cudaStreamSynchronize(st));
     } catch (...) {
       cudaStreamSynchronize(st);
-      for (void* p : {(void*)ra, (void*)rb, (void*)y, (void*)fr, (void*)fval, (void*)counts, stage}) A.put(p);
       throw;
     }
-    for (void* p : {(void*)ra, (void*)rb, (void*)y, (void*)fr, (void*)fval, (void*)counts, stage}) A.put(p);
   }
   if (info) {
     info->K = K;
@@ -306,60 +328,46 @@ void run_bidirectional(Graph& g, int32_t source, double alpha, double eps_r, dou
   cheb_coefficients(GP_FN_PPR, alpha, std::max(K, 1), c, tail);
   const size_t esz = out_dtype == GP_F64 ? 8 : 4;
   cudaStream_t st = g.stream;
-  Allocator& A = g.alloc;
-  const int64_t n = g.n, na = std::max<int64_t>(g.n_active, 1);
-  double* ra = (double*)A.get(sizeof(double) * n);
-  double* rb = (double*)A.get(sizeof(double) * n);
-  double* y = (double*)A.get(sizeof(double) * n);
-  const int64_t cap = na + g.nnz / kPushChunk + 1;
-  int2* fr = (int2*)A.get(sizeof(int2) * cap);
-  double* fval = (double*)A.get(sizeof(double) * cap);
-  int* counts = (int*)A.get(sizeof(int) * (K + 1));
-  unsigned long long* walks = (unsigned long long*)A.get(sizeof(unsigned long long));
-  void* stage = y_on_device ? nullptr : A.get(esz * n);
+  PushWork& w = push_work(g, !y_on_device);
+  const int64_t n = g.n;
+  double *ra = w.ra, *rb = w.rb, *y = w.y;
   unsigned long long h_walks = 0;
-  auto release = [&] {
-    for (void* p : {(void*)ra, (void*)rb, (void*)y, (void*)fr, (void*)fval, (void*)counts, (void*)walks, stage})
-      A.put(p);
-  };
   try {
     GP_CUDA_TRY(cudaMemsetAsync(ra, 0, sizeof(double) * n, st));
     GP_CUDA_TRY(cudaMemsetAsync(rb, 0, sizeof(double) * n, st));
     GP_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
-    GP_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (K + 1), st));
-    GP_CUDA_TRY(cudaMemsetAsync(walks, 0, sizeof(unsigned long long), st));
+    GP_CUDA_TRY(cudaMemsetAsync(w.counts, 0, sizeof(int) * (K + 1), st));
+    GP_CUDA_TRY(cudaMemsetAsync(w.walks, 0, sizeof(unsigned long long), st));
     const int64_t s = g.h_newid[source];
     const int grid = sms() * 8;
     // pi^ = ChebyPush(G, f, s, K, r_max); then r into ra (free after the push)
     if (g.rp64) {
-      run_push_rp<int64_t>(g, s, c, K, rmax, ra, rb, y, fr, fval, counts, nullptr);
+      run_push_rp<int64_t>(g, s, c, K, rmax, ra, rb, y, w.fr, w.fval, w.counts, nullptr);
       bidir_residual_kernel<int64_t><<<grid, 256, 0, st>>>(n, (const int64_t*)g.rp, g.ci, s, alpha, y, ra);
       GP_LAUNCHED();
       bidir_walk_kernel<int64_t><<<grid, 256, 0, st>>>(n, (const int64_t*)g.rp, g.ci, g.order, alpha, W, seed, ra,
-                                                       y, walks);
+                                                       y, w.walks);
     } else {
-      run_push_rp<int32_t>(g, s, c, K, rmax, ra, rb, y, fr, fval, counts, nullptr);
+      run_push_rp<int32_t>(g, s, c, K, rmax, ra, rb, y, w.fr, w.fval, w.counts, nullptr);
       bidir_residual_kernel<int32_t><<<grid, 256, 0, st>>>(n, (const int32_t*)g.rp, g.ci, s, alpha, y, ra);
       GP_LAUNCHED();
       bidir_walk_kernel<int32_t><<<grid, 256, 0, st>>>(n, (const int32_t*)g.rp, g.ci, g.order, alpha, W, seed, ra,
-                                                       y, walks);
+                                                       y, w.walks);
     }
     GP_LAUNCHED();
-    void* dst = y_on_device ? y_out : stage;
+    void* dst = y_on_device ? y_out : w.stage;
     if (out_dtype == GP_F64)
       push_output_kernel<double><<<sms() * 4, 256, 0, st>>>(g.n, g.newid, y, (double*)dst);
     else
       push_output_kernel<float><<<sms() * 4, 256, 0, st>>>(g.n, g.newid, y, (float*)dst);
     GP_LAUNCHED();
-    if (!y_on_device) GP_CUDA_TRY(cudaMemcpyAsync(y_out, stage, esz * g.n, cudaMemcpyDeviceToHost, st));
-    GP_CUDA_TRY(cudaMemcpyAsync(&h_walks, walks, sizeof(h_walks), cudaMemcpyDeviceToHost, st));
+    if (!y_on_device) GP_CUDA_TRY(cudaMemcpyAsync(y_out, w.stage, esz * g.n, cudaMemcpyDeviceToHost, st));
+    GP_CUDA_TRY(cudaMemcpyAsync(&h_walks, w.walks, sizeof(h_walks), cudaMemcpyDeviceToHost, st));
     GP_CUDA_TRY(cudaStreamSynchronize(st));
   } catch (...) {
     cudaStreamSynchronize(st);
-    release();
     throw;
   }
-  release();
   if (info) {
     info->K = K;
     info->k16_from = K + 1;
@@ -367,6 +375,14 @@ void run_bidirectional(Graph& g, int32_t source, double alpha, double eps_r, dou
     info->max_r_l1 = (double)h_walks;   // random walks run
     info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
+}
+
+void free_push_work(Graph& g) {
+  PushWork& w = g.pw;
+  for (void* p : {(void*)w.ra, (void*)w.rb, (void*)w.y, (void*)w.fr, (void*)w.fval, (void*)w.counts,
+                  (void*)w.walks, w.stage})
+    g.alloc.put(p);
+  w = PushWork{};
 }
 
 }  // namespace gp
