@@ -55,7 +55,7 @@ def test_hkpr_coefficients_bessel(t):
     assert np.max(np.abs(c - want)) < 1e-14
 
 
-def test_hkpr_survey_values():
+def test_hkpr_tabulated_bessel_values():
     # Tabulated modified Bessel values: e^-5 I_0(5) = 0.183541, 2 e^-5 I_1(5) = 0.327945
     # (six printed digits).
     c = O.cheb_coeffs("hkpr", 5.0, 2)
