@@ -19,10 +19,16 @@
 // the threshold decisions follow the FP64 reference.  Scanning every row
 // costs 8 bytes per row and iteration; the pushes cost what the frontier
 // holds.  The work vectors are allocated at the graph's first push query and
-// kept with the graph (PushWork), so a query allocates nothing.
+// kept with the graph (PushWork), so a query allocates nothing.  The
+// kernels read the query's source and (c_k, eps_k) from a small device block,
+// so the whole launch sequence of the push phase (memsets, init, K - 1 scans
+// and scatters) is captured once per K into a CUDA graph and replayed: one
+// launch per query instead of 2K, which is what bounds a query at large eps_a.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "gp_internal.h"
@@ -32,10 +38,22 @@ namespace gp {
 namespace {
 
 constexpr int kPushChunk = 2048;  // entries of one frontier item
+constexpr int kPushKCap = 1024;   // longest iteration count of a push query
+
+// A query's parameters, read by the kernels from device memory so that one
+// captured launch sequence per K serves every source and coefficient set:
+// the source (relabelled) and (c_k, eps_k) for k = 0..K.
+struct PushParams {
+  long long s;
+  long long pad;
+  double2 ce[kPushKCap + 1];
+};
 
 template <typename RP>
-__global__ void push_init_kernel(const RP* rp, const int32_t* ci, int64_t s, double c0, double* rcur, double* rnew,
+__global__ void push_init_kernel(const RP* rp, const int32_t* ci, const PushParams* pp, double* rcur, double* rnew,
                                  double* y) {
+  const int64_t s = pp->s;
+  const double c0 = pp->ce[0].x;
   const int64_t beg = rp[s], end = rp[s + 1];
   const double inv = 1.0 / (double)(end - beg);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -48,9 +66,10 @@ __global__ void push_init_kernel(const RP* rp, const int32_t* ci, int64_t s, dou
 
 // S_k: y += c_k r, r -> -r, and frontier items {u, chunk} with the pushed value.
 template <typename RP>
-__global__ void push_scan_kernel(int64_t n, const RP* rp, double* rcur, double* y, double ck, double eps,
+__global__ void push_scan_kernel(int64_t n, const RP* rp, double* rcur, double* y, const PushParams* pp, int k,
                                  int2* fr, double* fval, int* count) {
   const int lane = threadIdx.x & 31;
+  const double ck = pp->ce[k].x, eps = pp->ce[k].y;
   for (int64_t u0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; u0 < n;
        u0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = u0 + lane;
@@ -178,8 +197,6 @@ int sms() {
   return s > 0 ? s : 1;
 }
 
-constexpr int kPushKCap = 1024;  // longest iteration count of a push query
-
 // The graph's push work vectors (allocated once); the host-output staging
 // buffer only when a query writes to host memory.
 PushWork& push_work(Graph& g, bool need_stage) {
@@ -210,32 +227,105 @@ PushWork& push_work(Graph& g, bool need_stage) {
   return w;
 }
 
+// Per graph: the pinned and device copies of the query parameters and one
+// instantiated CUDA graph per iteration count K (the launch sequence below,
+// captured once; the work vectors are the graph's and do not move).  Kept
+// beside the graph's PushWork and released with it.
+struct PushGraphs {
+  PushParams* h = nullptr;  // pinned host
+  PushParams* d = nullptr;  // device
+  int* h_counts = nullptr;  // pinned host copy of the frontier sizes
+  std::map<int, cudaGraphExec_t> exec;
+};
+std::mutex g_push_mu;
+std::map<const Graph*, PushGraphs> g_push;
+
+PushGraphs& push_graphs(Graph& g) {
+  std::lock_guard<std::mutex> lk(g_push_mu);
+  PushGraphs& pg = g_push[&g];
+  if (!pg.h) {
+    GP_CUDA_TRY(cudaHostAlloc((void**)&pg.h, sizeof(PushParams), cudaHostAllocDefault));
+    GP_CUDA_TRY(cudaHostAlloc((void**)&pg.h_counts, sizeof(int) * (kPushKCap + 1), cudaHostAllocDefault));
+    pg.d = (PushParams*)g.alloc.get(sizeof(PushParams));
+  }
+  return pg;
+}
+
+// The push phase of one query: zero the vectors, y = c_0 e_s, r_cur = P e_s,
+// r_new = -e_s, then K - 1 iterations of scan + scatter (the vectors swap
+// roles each iteration; y ends in w.y).  Stream-ordered on g.stream; no
+// allocation and no synchronisation, so it can be captured.
 template <typename RP>
-void run_push_rp(Graph& g, int64_t s, const std::vector<double>& c, int K, double eps_a, double* rcur, double* rnew,
-                 double* y, int2* fr, double* fval, int* counts, int64_t* pushed) {
+void push_sequence(Graph& g, PushWork& w, const PushParams* pp, int K) {
   cudaStream_t st = g.stream;
   const RP* rp = (const RP*)g.rp;
-  push_init_kernel<RP><<<4, 256, 0, st>>>(rp, g.ci, s, c[0], rcur, rnew, y);
-  GP_LAUNCHED();
+  const int64_t n = std::max<int64_t>(g.n, 1);
+  GP_CUDA_TRY(cudaMemsetAsync(w.ra, 0, sizeof(double) * n, st));
+  GP_CUDA_TRY(cudaMemsetAsync(w.rb, 0, sizeof(double) * n, st));
+  GP_CUDA_TRY(cudaMemsetAsync(w.y, 0, sizeof(double) * n, st));
+  GP_CUDA_TRY(cudaMemsetAsync(w.counts, 0, sizeof(int) * (K + 1), st));
+  double *rcur = w.ra, *rnew = w.rb;
+  push_init_kernel<RP><<<4, 256, 0, st>>>(rp, g.ci, pp, rcur, rnew, w.y);
+  GP_CUDA_TRY(cudaGetLastError());
   const int grid = sms() * 8;
   for (int k = 1; k < K; ++k) {
-    double tailK = 0.0;
-    for (int l = k; l <= K; ++l) tailK += std::fabs(c[l]);
-    const double eps = tailK > 0.0 ? eps_a / (4.0 * K * tailK) : 0.0;
-    push_scan_kernel<RP><<<grid, 256, 0, st>>>(g.n, rp, rcur, y, c[k], eps, fr, fval, counts + k);
-    GP_LAUNCHED();
-    push_scatter_kernel<RP><<<grid, 256, 0, st>>>(rp, g.ci, fr, fval, counts + k, rnew);
-    GP_LAUNCHED();
+    push_scan_kernel<RP><<<grid, 256, 0, st>>>(g.n, rp, rcur, w.y, pp, k, w.fr, w.fval, w.counts + k);
+    GP_CUDA_TRY(cudaGetLastError());
+    push_scatter_kernel<RP><<<grid, 256, 0, st>>>(rp, g.ci, w.fr, w.fval, w.counts + k, rnew);
+    GP_CUDA_TRY(cudaGetLastError());
     std::swap(rcur, rnew);
   }
-  if (pushed) {
-    std::vector<int> h(K + 1, 0);
-    GP_CUDA_TRY(cudaMemcpyAsync(h.data(), counts, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, st));
-    GP_CUDA_TRY(cudaStreamSynchronize(st));
-    int64_t tot = 0;
-    for (int k = 1; k < K; ++k) tot += h[k];
-    *pushed = tot;
+}
+
+// Run the push phase for source s (relabelled) with thresholds
+// eps_k = eps_a / (4 K sum_{l=k}^K |c_l|): upload the parameters, then replay
+// the graph captured for this K (capturing it on first use).
+void run_push(Graph& g, PushWork& w, int64_t s, const std::vector<double>& c, int K, double eps_a) {
+  PushGraphs& pg = push_graphs(g);
+  pg.h->s = (long long)s;
+  pg.h->pad = 0;
+  for (int k = 0; k <= K; ++k) {
+    double tailK = 0.0;
+    for (int l = k; l <= K; ++l) tailK += std::fabs(c[l]);
+    pg.h->ce[k] = make_double2(c[k], k >= 1 && tailK > 0.0 ? eps_a / (4.0 * K * tailK) : 0.0);
   }
+  cudaStream_t st = g.stream;
+  GP_CUDA_TRY(cudaMemcpyAsync(pg.d, pg.h, 16 + sizeof(double2) * (K + 1), cudaMemcpyHostToDevice, st));
+  auto it = pg.exec.find(K);
+  if (it == pg.exec.end()) {
+    cudaGraph_t graph = nullptr;
+    GP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      if (g.rp64)
+        push_sequence<int64_t>(g, w, pg.d, K);
+      else
+        push_sequence<int32_t>(g, w, pg.d, K);
+    } catch (...) {
+      cudaStreamEndCapture(st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    GP_CUDA_TRY(cudaStreamEndCapture(st, &graph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    GP_CUDA_TRY(e);
+    it = pg.exec.emplace(K, exec).first;
+  }
+  GP_CUDA_TRY(cudaGraphLaunch(it->second, st));
+  count_launch(1 + 2 * (uint64_t)(K - 1));
+}
+
+void free_push_graphs(Graph& g) {
+  std::lock_guard<std::mutex> lk(g_push_mu);
+  auto it = g_push.find(&g);
+  if (it == g_push.end()) return;
+  PushGraphs& pg = it->second;
+  for (auto& kv : pg.exec) cudaGraphExecDestroy(kv.second);
+  if (pg.h) cudaFreeHost(pg.h);
+  if (pg.h_counts) cudaFreeHost(pg.h_counts);
+  g.alloc.put(pg.d);
+  g_push.erase(it);
 }
 
 }  // namespace
@@ -277,17 +367,8 @@ void run_chebypush(Graph& g, int function, int32_t source, double param, double 
     GP_CUDA_TRY(cudaStreamSynchronize(st));
   } else {
     PushWork& w = push_work(g, !y_on_device);
-    const int64_t n = std::max<int64_t>(g.n, 1);
     try {
-      GP_CUDA_TRY(cudaMemsetAsync(w.ra, 0, sizeof(double) * n, st));
-      GP_CUDA_TRY(cudaMemsetAsync(w.rb, 0, sizeof(double) * n, st));
-      GP_CUDA_TRY(cudaMemsetAsync(w.y, 0, sizeof(double) * n, st));
-      GP_CUDA_TRY(cudaMemsetAsync(w.counts, 0, sizeof(int) * (K + 1), st));
-      const int64_t s = g.h_newid[source];
-      if (g.rp64)
-        run_push_rp<int64_t>(g, s, c, K, eps_a, w.ra, w.rb, w.y, w.fr, w.fval, w.counts, &pushed);
-      else
-        run_push_rp<int32_t>(g, s, c, K, eps_a, w.ra, w.rb, w.y, w.fr, w.fval, w.counts, &pushed);
+      run_push(g, w, g.h_newid[source], c, K, eps_a);
       void* dst = y_on_device ? y_out : w.stage;
       const int grid = sms() * 4;
       if (out_dtype == GP_F64)
@@ -296,7 +377,10 @@ void run_chebypush(Graph& g, int function, int32_t source, double param, double 
         push_output_kernel<float><<<grid, 256, 0, st>>>(g.n, g.newid, w.y, (float*)dst);
       GP_LAUNCHED();
       if (!y_on_device) GP_CUDA_TRY(cudaMemcpyAsync(y_out, w.stage, esz * g.n, cudaMemcpyDeviceToHost, st));
+      PushGraphs& pg = push_graphs(g);
+      GP_CUDA_TRY(cudaMemcpyAsync(pg.h_counts, w.counts, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, st));
       GP_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int k = 1; k < K; ++k) pushed += pg.h_counts[k];
     } catch (...) {
       cudaStreamSynchronize(st);
       throw;
@@ -330,25 +414,20 @@ void run_bidirectional(Graph& g, int32_t source, double alpha, double eps_r, dou
   cudaStream_t st = g.stream;
   PushWork& w = push_work(g, !y_on_device);
   const int64_t n = g.n;
-  double *ra = w.ra, *rb = w.rb, *y = w.y;
+  double *ra = w.ra, *y = w.y;
   unsigned long long h_walks = 0;
   try {
-    GP_CUDA_TRY(cudaMemsetAsync(ra, 0, sizeof(double) * n, st));
-    GP_CUDA_TRY(cudaMemsetAsync(rb, 0, sizeof(double) * n, st));
-    GP_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
-    GP_CUDA_TRY(cudaMemsetAsync(w.counts, 0, sizeof(int) * (K + 1), st));
-    GP_CUDA_TRY(cudaMemsetAsync(w.walks, 0, sizeof(unsigned long long), st));
     const int64_t s = g.h_newid[source];
     const int grid = sms() * 8;
     // pi^ = ChebyPush(G, f, s, K, r_max); then r into ra (free after the push)
+    run_push(g, w, s, c, K, rmax);
+    GP_CUDA_TRY(cudaMemsetAsync(w.walks, 0, sizeof(unsigned long long), st));
     if (g.rp64) {
-      run_push_rp<int64_t>(g, s, c, K, rmax, ra, rb, y, w.fr, w.fval, w.counts, nullptr);
       bidir_residual_kernel<int64_t><<<grid, 256, 0, st>>>(n, (const int64_t*)g.rp, g.ci, s, alpha, y, ra);
       GP_LAUNCHED();
       bidir_walk_kernel<int64_t><<<grid, 256, 0, st>>>(n, (const int64_t*)g.rp, g.ci, g.order, alpha, W, seed, ra,
                                                        y, w.walks);
     } else {
-      run_push_rp<int32_t>(g, s, c, K, rmax, ra, rb, y, w.fr, w.fval, w.counts, nullptr);
       bidir_residual_kernel<int32_t><<<grid, 256, 0, st>>>(n, (const int32_t*)g.rp, g.ci, s, alpha, y, ra);
       GP_LAUNCHED();
       bidir_walk_kernel<int32_t><<<grid, 256, 0, st>>>(n, (const int32_t*)g.rp, g.ci, g.order, alpha, W, seed, ra,
@@ -378,6 +457,7 @@ void run_bidirectional(Graph& g, int32_t source, double alpha, double eps_r, dou
 }
 
 void free_push_work(Graph& g) {
+  free_push_graphs(g);
   PushWork& w = g.pw;
   for (void* p : {(void*)w.ra, (void*)w.rb, (void*)w.y, (void*)w.fr, (void*)w.fval, (void*)w.counts,
                   (void*)w.walks, w.stage})
