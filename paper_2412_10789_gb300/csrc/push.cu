@@ -42,10 +42,14 @@ constexpr int kPushKCap = 1024;   // longest iteration count of a push query
 
 // A query's parameters, read by the kernels from device memory so that one
 // captured launch sequence per K serves every source and coefficient set:
-// the source (relabelled) and (c_k, eps_k) for k = 0..K.
+// the source (relabelled), the rows the scans cover, and (c_k, eps_k) for
+// k = 0..K.  Only rows with neighbours can hold a residual unless the source
+// itself is isolated (or an asymmetric CSR lists edges into rows without
+// neighbours), so the scans cover the non-isolated prefix of the relabelled
+// rows (isolated rows come last), or else all rows.
 struct PushParams {
   long long s;
-  long long pad;
+  long long rows;
   double2 ce[kPushKCap + 1];
 };
 
@@ -66,9 +70,10 @@ __global__ void push_init_kernel(const RP* rp, const int32_t* ci, const PushPara
 
 // S_k: y += c_k r, r -> -r, and frontier items {u, chunk} with the pushed value.
 template <typename RP>
-__global__ void push_scan_kernel(int64_t n, const RP* rp, double* rcur, double* y, const PushParams* pp, int k,
-                                 int2* fr, double* fval, int* count) {
+__global__ void push_scan_kernel(const RP* rp, double* rcur, double* y, const PushParams* pp, int k, int2* fr,
+                                 double* fval, int* count) {
   const int lane = threadIdx.x & 31;
+  const int64_t n = pp->rows;
   const double ck = pp->ce[k].x, eps = pp->ce[k].y;
   for (int64_t u0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; u0 < n;
        u0 += (int64_t)gridDim.x * blockDim.x) {
@@ -269,7 +274,7 @@ void push_sequence(Graph& g, PushWork& w, const PushParams* pp, int K) {
   GP_CUDA_TRY(cudaGetLastError());
   const int grid = sms() * 8;
   for (int k = 1; k < K; ++k) {
-    push_scan_kernel<RP><<<grid, 256, 0, st>>>(g.n, rp, rcur, w.y, pp, k, w.fr, w.fval, w.counts + k);
+    push_scan_kernel<RP><<<grid, 256, 0, st>>>(rp, rcur, w.y, pp, k, w.fr, w.fval, w.counts + k);
     GP_CUDA_TRY(cudaGetLastError());
     push_scatter_kernel<RP><<<grid, 256, 0, st>>>(rp, g.ci, w.fr, w.fval, w.counts + k, rnew);
     GP_CUDA_TRY(cudaGetLastError());
@@ -283,7 +288,8 @@ void push_sequence(Graph& g, PushWork& w, const PushParams* pp, int K) {
 void run_push(Graph& g, PushWork& w, int64_t s, const std::vector<double>& c, int K, double eps_a) {
   PushGraphs& pg = push_graphs(g);
   pg.h->s = (long long)s;
-  pg.h->pad = 0;
+  // (an unvalidated asymmetric CSR can push into rows without neighbours)
+  pg.h->rows = s < g.n_active && !g.ci_beyond_active ? (long long)g.n_active : (long long)g.n;
   for (int k = 0; k <= K; ++k) {
     double tailK = 0.0;
     for (int l = k; l <= K; ++l) tailK += std::fabs(c[l]);

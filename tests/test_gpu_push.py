@@ -184,3 +184,34 @@ def test_int64_row_offsets(gp):
             assert e["l1"] <= 1e-6 and e["maxabs"] <= 1e-7 + 15 * 2.0 ** -24 * np.abs(want).max(), e
     finally:
         dg.close()
+
+
+def test_chebypush_unvalidated_asymmetric_csr(gp):
+    """Rows that list nodes without neighbours (asymmetric CSR, symmetry check
+    off): pushes reach those nodes, which hold residual but push nothing, on
+    the device as in the oracle's Algorithm 4."""
+    import torch
+    base = gg.rmat(10, 8, seed=5)
+    rows = [list(base.col_idx[base.row_ptr[u]:base.row_ptr[u + 1]]) for u in range(base.n)]
+    iso = [u for u in range(base.n) if not rows[u]]
+    assert len(iso) >= 3
+    for k, u in enumerate([u for u in range(base.n) if rows[u]][:40]):
+        rows[u] = sorted(set(rows[u]) | {iso[k % len(iso)]})
+    rp = np.zeros(base.n + 1, dtype=np.int64)
+    for u in range(base.n):
+        rp[u + 1] = rp[u] + len(rows[u])
+    ci = np.array([v for r in rows for v in r], dtype=np.int32)
+    g = gg.Graph("rmat10_with_isolated_targets", base.n, rp, ci)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, validate_symmetry=0)
+    try:
+        y = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        for s in [u for u in range(g.n) if rows[u]][:3]:
+            info = gp.gp_chebypush(dg, 0, int(s), 0.2, 1e-6, y)
+            K, c = _oracle_K("ppr", 0.2, 1e-6)
+            assert info["K"] == K
+            want = O.chebypush(g, int(s), "ppr", 0.2, K, eps_a=1e-6, coeffs=c[:K + 1])
+            got = y.cpu().numpy()
+            assert np.max(np.abs(got - want)) <= 1e-12, (s, np.max(np.abs(got - want)))
+            assert np.any(want[iso] != 0.0)  # the isolated targets did take residual
+    finally:
+        dg.close()
