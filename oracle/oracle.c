@@ -200,12 +200,13 @@ int or_chebypush(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int6
   double* rnew = rb;
   for (int64_t u = 0; u < n; ++u) y[u] = 0.0;
   y[s] = c[0];
+  /* r_1 = P e_s, as the pushes below move residual: 1/d_s to every node in
+   * the neighbour list of s (on the undirected graphs of Section 2.1 this is
+   * the column s of P; for a CSR that is not symmetric it keeps the first
+   * step and the iterations one operation) */
   {
-    double* es = (double*)calloc((size_t)n, sizeof(double));
-    if (!es) { free(ra); free(rb); return 2; }
-    es[s] = 1.0;
-    or_P_apply(n, row_ptr, col_idx, es, rcur);
-    free(es);
+    const double ds = deg_of(row_ptr, s);
+    for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) rcur[col_idx[e]] += 1.0 / ds;
   }
   rnew[s] = -1.0;
   for (int k = 1; k < K; ++k) {
