@@ -259,7 +259,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        # raw samples: GP_CLOCKS_DIR if set, else the system temporary directory
+        # raw samples: kept in GP_CLOCKS_DIR if set, else a temporary file
+        self.keep = bool(os.environ.get("GP_CLOCKS_DIR"))
         base = os.environ.get("GP_CLOCKS_DIR") or tempfile.gettempdir()
         self.path = os.path.join(base, f"clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
@@ -297,6 +298,11 @@ class ClockSampler:
                 for name, val in zip(names, parts[5:9]):
                     if val.lower().startswith("active"):
                         reasons.add(name)
+        if not self.keep:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
