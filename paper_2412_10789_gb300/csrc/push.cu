@@ -351,13 +351,19 @@ void run_chebypush(Graph& g, int function, int32_t source, double param, double 
   auto t0 = std::chrono::steady_clock::now();
   // K: Algorithm 4 adds c_0 .. c_{K-1}; by default the smallest K whose
   // truncation tail(K-1) = sum_{l>=K} |c_l| is at most eps_a / 2 (Theorem 3)
+  // (coefficients up to 128 first: the usual K is far below, and the table
+  // costs host time on every query)
   std::vector<double> c, tail;
-  cheb_coefficients(function, param, 1024, c, tail);
+  const int kc = K > 0 ? K : 128;
+  cheb_coefficients(function, param, kc, c, tail);
   if (K == 0) {
     K = 1;
-    while (K < 1024 && tail[K - 1] > eps_a / 2) ++K;
+    while (K < kc && tail[K - 1] > eps_a / 2) ++K;
+    if (tail[K - 1] > eps_a / 2) {
+      cheb_coefficients(function, param, 1024, c, tail);
+      while (K < 1024 && tail[K - 1] > eps_a / 2) ++K;
+    }
   }
-  K = std::max(K, 1);
   const size_t esz = out_dtype == GP_F64 ? 8 : 4;
   cudaStream_t st = g.stream;
   int64_t pushed = 0;
