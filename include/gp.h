@@ -84,7 +84,7 @@ typedef struct {
                               keep T_k as float pairs (~48 bits) instead of FP32: FP32 rounding
                               is not damped on tiny graphs with unit-modulus eigenvalues
                               (0: default 1024; -1: never) */
-  double warmup_tail;      /* 16-bit storage only once tail(k) < warmup_tail (default 1e-2) */
+  double warmup_tail;      /* 16-bit storage only once sum_m (m+1)|c_{k+1+m}| < warmup_tail (default 1e-2) */
   size_t mem_budget;       /* bytes the serving loop may use for column blocks (0: 80% of free) */
   void* (*alloc)(size_t bytes, void* ctx); /* device allocator; NULL: cudaMalloc */
   void (*free)(void* ptr, void* ctx);      /* its release function */

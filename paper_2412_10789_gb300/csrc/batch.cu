@@ -27,10 +27,10 @@
 // at global pass g gets Q_1 in buffer g&1 and Q_0 in buffer (g+1)&1, so every
 // pass reads buffer g&1 and writes buffer (g+1)&1 for all columns.
 //
-// Storage.  BF16/FP16 storage follows a warm-up schedule (Lemma 5: a rounding
-// error made at step l reaches y weighted by sum_{k>=l} |c_k|): passes run in
-// FP32 while any column's tail is at least warmup_tail, then two transition
-// passes (FP32 -> 16-bit) and 16-bit from there on.  FP16 stores Q * 2^12 to
+// Storage.  BF16/FP16 storage follows a warm-up schedule: passes run in FP32
+// while any column's weight W(k) is at least warmup_tail, then two transition
+// passes (FP32 -> 16-bit) and 16-bit from there on.  W(k) is the weight with
+// which a rounding error of step k reaches y (warm_step below).  FP16 stores Q * 2^12 to
 // keep small values of Q = r/d above FP16's subnormal range.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -1178,6 +1178,26 @@ void launch_stage(const SpmmArgs& a, int stage, cudaStream_t st) {
 
 // ------------------------------------------------------------------ engine
 
+namespace {
+// The first step whose Q may be stored in 16 bits: the smallest k with
+// W(k) = sum_{m>=0} (m + 1) |c_{k+1+m}| < warmup_tail.  A rounding error that
+// the recurrence does not compensate propagates with the second-kind
+// polynomials U_m(P) (the residual-propagation lemma of the generalized subset
+// recurrence, with no compensation), and |U_m| <= m + 1 on [-1, 1], so an
+// error made at step k reaches y weighted by W(k) rather than by the tail
+// sum_{l>k} |c_l| (which let slowly decaying expansions, SSPPR alpha = 0.1,
+// pass l1 = 1e-4 in 16-bit blocks).  kcap when no step qualifies.
+int warm_step(const std::vector<double>& c, int kcap, double warmup_tail) {
+  const int last = (int)c.size() - 1;
+  for (int k = 0; k <= kcap && k < kMaxColK; ++k) {
+    double w = 0.0;
+    for (int l = k + 1; l <= last; ++l) w += (double)(l - k) * std::fabs(c[l]);
+    if (w < warmup_tail) return k;
+  }
+  return std::min(kcap, kMaxColK - 1);
+}
+}  // namespace
+
 ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long)
     : g_(g), B_(B), bw_(B), storage_(storage), st_(st) {
   if (B < 8 || B > 256 || (B & (B - 1)))
@@ -1350,12 +1370,7 @@ std::vector<int> ColumnEngine::admit(const std::vector<gp_request>& reqs, std::v
     p.kstop = r.k_rule == GP_K_FIXED ? r.k_fixed
               : r.k_rule == GP_K_PAPER ? std::min(kcap - 1, paper_k(r.function, r.param, r.l1_tol))
                                        : 0;
-    p.warm = 0;
-    for (int k = 0; k <= kcap && k < kMaxColK; ++k)
-      if (tail[k] < g_.cfg.warmup_tail) {
-        p.warm = k;
-        break;
-      }
+    p.warm = warm_step(c, kcap, g_.cfg.warmup_tail);
     params.push_back(p);
     cols.push_back(slot);
     srcs.push_back(g_.h_newid[r.source]);
@@ -2165,12 +2180,7 @@ std::vector<ColumnEngine::Finished> ColumnEngine::propagate(const float* X, floa
   }
   p.tol = (float)(tol / kCMargin);
   p.kstop = 0;
-  p.warm = 0;
-  for (int k = 0; k <= kcap_ && k < kMaxColK; ++k)
-    if (tail[k] < g_.cfg.warmup_tail) {
-      p.warm = k;
-      break;
-    }
+  p.warm = warm_step(c, kcap_, g_.cfg.warmup_tail);
   std::vector<ColState> cs(B_, ColState{0, 0.f});
   std::vector<ColParam> par(B_, p);
   std::vector<ColStat> st(B_, ColStat{0, 0, 0, 0.f});

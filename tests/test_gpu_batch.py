@@ -146,6 +146,27 @@ def test_batch_fp32_wide_blocks_meet_1e6(gp, gname, B):
         dg.close()
 
 
+@pytest.mark.parametrize("fn,param", [(0, 0.1), (1, 10.0)])
+def test_batch_bf16_homogeneous_slow_decay(gp, fn, param):
+    """A BF16 block of only slowly decaying expansions (SSPPR alpha = 0.1, HKPR
+    t = 10) switches to 16 bits at its own, early warm-up step; the weight of
+    that switch counts the linear growth of uncompensated rounding errors, and
+    every column stays within l1 <= 1e-4."""
+    g = graph("rmat14")
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16, storage=gp.GP_BF16)
+    try:
+        srcs = gg.sources(g, 16, 21)
+        ys = _outputs(g, len(srcs))
+        infos = gp.gp_batch(dg, [gp.make_request(fn, int(s), param, 1e-4, ys[i]) for i, s in enumerate(srcs)])
+        for i, s in enumerate(srcs):
+            ystar = O.chebypower(g, int(s), KINDS[fn], param, 150)
+            l1 = O.errors(g, ystar, ys[i].cpu().numpy())["l1"]
+            assert l1 <= 1e-4, (i, l1, infos[i])
+            assert infos[i]["k16_from"] <= infos[i]["K"]  # the 16-bit phase did run
+    finally:
+        dg.close()
+
+
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 def test_batch_narrow_16bit_block(gp, storage):
     """Eight columns per block: lanes own 8 columns and the FP32 -> 16-bit
