@@ -25,7 +25,7 @@ struct ColParam {
   float tail[kMaxColK];  // tail(k) = sum_{l>k} |c_l|
   float tol;             // l1 tolerance over kCMargin: stop at tail(k) * C <= tol (< 0: no rule)
   int kstop;             // fixed K (> 0) or 0
-  int warm;              // first k with tail(k) < warmup_tail
+  int warm;              // first k with W(k) < warmup_tail (warm_step in batch.cu)
   int pad;
 };
 
