@@ -54,11 +54,16 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--power-baseline", action="store_true", help="also time the GPU PwMethod")
+    p.add_argument("--no-power-baseline", action="store_true", help="skip the GPU PwMethod leg")
     p.add_argument("--no-batched", action="store_true", help="skip the batched and served forms")
     p.add_argument("--batch-width", type=int, default=128)
     p.add_argument("--forms", default="single,batched,serving",
-                   help="comma list of the forms to time (the single-source form is always run)")
+                   help="comma list of the forms to time (without 'single' only the named forms run, for "
+                        "profiling; the line's value is then null)")
+    p.add_argument("--serve-requests", type=int, default=512,
+                   help="rmat22 serving leg: requests per arrival pattern")
+    p.add_argument("--cpu-sample", type=int, default=4,
+                   help="queries whose GPU outputs are checked against the converged FP64 oracle")
     p.add_argument("--batch-storage", default="bf16,fp32", help="storages of the batched form")
     p.add_argument("--batch-reps", type=int, default=3)
     p.add_argument("--workload", default="rmat22",
@@ -74,7 +79,11 @@ def parse():
 
 
 BATCH_FORMS = {"bf16": ("bf16_tol1e-4", "GP_BF16", 1e-4), "fp16": ("fp16_tol1e-4", "GP_F16", 1e-4),
-               "fp32": ("fp32_tol1e-6", "GP_F32", 1e-6), "fp32_1e-4": ("fp32_tol1e-4", "GP_F32", 1e-4)}
+               "fp32": ("fp32_fp32y_tol1e-6", "GP_F32", 1e-6), "fp32_1e-4": ("fp32_fp32y_tol1e-4", "GP_F32", 1e-4)}
+# The batched FP32 form accumulates y in FP32 (rounded once per step), so its
+# element-wise bar is max-abs <= 1e-7 + K 2^-24 max|y| at fixed K, not the single
+# form's 1e-8 (which needs the float-pair y of the single-query kernel).
+FP32Y_BAR = "l1 <= tol against the converged oracle; max-abs <= 1e-7 + K*2^-24*max|y| at fixed K (FP32 y)"
 
 
 def time_single(gp, dg, queries, tol, dev):
@@ -89,14 +98,19 @@ def time_single(gp, dg, queries, tol, dev):
     return len(queries) / (time.perf_counter() - t0)
 
 
+def _host(y):
+    return y.detach().cpu().numpy().astype(np.float64)
+
+
 def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32"), reps=3, width=128,
-                  single_value=None, single_tol=1e-6):
+                  single_value=None, single_tol=1e-6, sample=()):
     """gp_batch over the step's queries in blocks of `width` columns: BF16/FP16
     storage (FP32 warm-up) at l1 <= 1e-4, FP32 storage at l1 <= 1e-6;
     queries/s over `reps` runs, and the ratio to the single-source form at
-    the same tolerance on the same queries."""
+    the same tolerance on the same queries.  Returns (results, outputs of the
+    `sample` queries per result, with their tolerance and K)."""
     import torch
-    res = {}
+    res, outs = {}, {}
     single = {single_tol: single_value} if single_value else {}
     for key in storages:
         name, storage_name, tol = BATCH_FORMS[key]
@@ -116,19 +130,22 @@ def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32
         dt = dist_max(time.perf_counter() - t0, world, dev)
         prof = gp.gp_profile_read(dg)
         gp.gp_profile_enable(dg, False)
+        outs[name] = {"tol": tol, "y": {i: _host(ys[i]) for i in sample}, "K": {i: infos[i]["K"] for i in sample}}
         value = len(queries) * reps * world / dt
         if tol not in single:  # whole-job rate: every rank at the slowest rank's pace
             single[tol] = world / dist_max(1.0 / time_single(gp, dg_single, queries, tol, dev), world, dev)
         peak, peak_kind = measured_peaks()
         ms = prof["step_ms"] / max(prof["step_launches"], 1)
         achieved = prof["step_bytes"] / max(prof["step_launches"], 1) / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
-        res[name] = {"value": value, "unit": UNIT, "block_width": width, "queries": len(queries),
+        res[name] = {"value": value, "unit": UNIT, "l1_tol": tol, "block_width": width, "queries": len(queries),
                      "mean_K": float(np.mean([i["K"] for i in infos])),
                      "single_source_same_tol": single[tol], "vs_single_source_same_tol": value / single[tol],
                      "roofline": {"bound": "hbm", "kernel": "spmm_step_kernel", "achieved": achieved, "peak": peak,
                                   "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                                   "mean_launch_ms": ms, "launches": prof["step_launches"],
                                   "spmm_share_of_wall": prof["step_ms"] / 1000.0 / dt}}
+        if storage == gp.GP_F32:
+            res[name]["bar"] = FP32Y_BAR
         if key == "fp32":
             # Clenshaw's backward form of the same sums, each column at the K the forward form chose
             kreqs = [gp.make_request(fn, s, p, tol, ys[i], k_rule=gp.GP_K_FIXED, k_fixed=max(1, infos[i]["K"]))
@@ -140,48 +157,85 @@ def bench_batched(gp, dg_single, g, queries, dev, world, storages=("bf16", "fp32
                 gp.gp_batch_clenshaw(dg, kreqs)
             torch.cuda.synchronize()
             dtc = dist_max(time.perf_counter() - t0, world, dev)
-            res["fp32_clenshaw_same_K"] = {"value": len(queries) * reps * world / dtc, "unit": UNIT,
+            res["fp32_clenshaw_same_K"] = {"value": len(queries) * reps * world / dtc, "unit": UNIT, "l1_tol": tol,
                                            "block_width": width, "queries": len(queries),
-                                           "K": "per column, the forward form's K at l1 <= 1e-6"}
+                                           "K": "per column, the forward form's K at l1 <= 1e-6", "bar": FP32Y_BAR}
+            outs["fp32_clenshaw_same_K"] = {"tol": tol, "y": {i: _host(ys[i]) for i in sample},
+                                            "K": {i: infos[i]["K"] for i in sample}}
         dg.close()
         del ys
-    return res
+    return res, outs
 
 
-def bench_serving(gp, g, queries, dev, world, reps=2):
-    """The step's queries through gp_submit/gp_poll, all submitted at once, with
-    l1 tolerances cycling over 1e-4, 1e-5, 1e-6: queries/s and latency
-    (submit to completion) percentiles."""
+def serve_run(gp, dg, specs, arrivals, pool, keep=()):
+    """Submit request i = (function, source, param, tol) at arrivals[i] seconds
+    from the start through gp_submit and collect it with gp_poll; outputs go to
+    buffers of `pool` (reused as requests complete), except the requests in
+    `keep`, which get buffers of their own.  Returns (wall seconds, latencies
+    in ms as the service measured them, {i: output of a kept request})."""
     import torch
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=min(256, len(queries)))
-    ys = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in queries]
-    tols = [1e-4, 1e-5, 1e-6]
-    reqs = [gp.make_request(fn, s, p, tols[i % 3], ys[i]) for i, (fn, s, p) in enumerate(queries)]
-
-    def run_once():
-        tickets = [gp.gp_submit(dg, r) for r in reqs]
-        infos = [None] * len(tickets)
-        left = len(tickets)
-        while left:
-            for j, t in enumerate(tickets):
-                if infos[j] is None:
-                    infos[j] = gp.gp_poll(dg, t)
-                    left -= infos[j] is not None
-            time.sleep(0.0005)
-        return infos
-
-    run_once()  # warm-up
-    dist_barrier(world)
-    lat = []
+    free = list(range(len(pool)))
+    kept = {i: torch.empty_like(pool[0]) for i in keep}
+    pending, lat = {}, []
     t0 = time.perf_counter()
-    for _ in range(reps):
-        lat += [i["ms"] for i in run_once()]
-    dt = dist_max(time.perf_counter() - t0, world, dev)
+    i, n = 0, len(specs)
+    while i < n or pending:
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i] <= now and (free or i in kept):
+            fn, s, p, tol = specs[i]
+            b = -1 if i in kept else free.pop()
+            r = gp.make_request(int(fn), int(s), float(p), float(tol), kept[i] if b < 0 else pool[b])
+            pending[gp.gp_submit(dg, r)] = b
+            i += 1
+        for tk in list(pending):
+            inf = gp.gp_poll(dg, tk)
+            if inf is not None:
+                lat.append(inf["ms"])
+                b = pending.pop(tk)
+                if b >= 0:
+                    free.append(b)
+        time.sleep(0.0002)
+    return time.perf_counter() - t0, lat, kept
+
+
+def serve_levels(gp, dg, specs, pool, loads, seed, keep=()):
+    """The saturated rate (every request submitted at once), then Poisson
+    arrivals at each offered load as a fraction of it."""
+    rng = np.random.default_rng(seed)
+    n = len(specs)
+    serve_run(gp, dg, specs[: min(n, 64)], np.zeros(min(n, 64)), pool)  # warm-up
+    wall, lat, kept = serve_run(gp, dg, specs, np.zeros(n), pool, keep)
+    sat = n / wall
+    res = {"saturated": {"value": sat, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "requests": n}}
+    for load in loads:
+        gaps = rng.exponential(1.0 / (load * sat), n)
+        wall, lat, _ = serve_run(gp, dg, specs, np.cumsum(gaps), pool)
+        res[f"load_{load:g}"] = {"offered": load * sat, "value": n / wall, "unit": UNIT,
+                                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                 "requests": n}
     stats = gp.gp_serve_stats(dg)
+    res["mean_active_columns"] = stats["mean_active"]
+    return res, kept
+
+
+def bench_serving(gp, g, queries, dev, world, nreq=512, loads=(0.5, 0.8, 0.95), sample=()):
+    """The step's queries through gp_submit/gp_poll (continuous batching), l1
+    tolerances cycling over 1e-4, 1e-5, 1e-6: the saturated rate, then Poisson
+    arrivals at 50/80/95% of it, with p50/p99 latency (arrival to completion)."""
+    import torch
+    width = 256
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=width)
+    tols = [1e-4, 1e-5, 1e-6]
+    specs = [queries[i % len(queries)] + (tols[i % 3],) for i in range(nreq)]
+    pool = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range(width + 64)]
+    dist_barrier(world)
+    res, kept = serve_levels(gp, dg, specs, pool, loads, 7, keep=sample)
     dg.close()
-    return {"value": len(queries) * reps * world / dt, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_active_columns": stats["mean_active"],
-            "storage": "fp32", "arrivals": "all queries of a step submitted at once"}
+    res.update({"storage": "fp32", "block_width": width, "workload": "the step's queries, tolerances 1e-4/1e-5/1e-6",
+                "arrivals": "saturated: all at once; load_x: Poisson at x times the saturated rate"})
+    outs = {"serving": {"tol": {i: specs[i][3] for i in sample}, "y": {i: _host(kept[i]) for i in sample}}}
+    return res, outs
 
 
 # ----------------------------------------------------------------- distributed helpers
@@ -226,6 +280,23 @@ def workload(scale, nsrc):
     return g, queries
 
 
+# Source files each profiled kernel is built from; the committed ncu figures
+# carry a hash of them and are reported only while it still matches.
+KERNEL_SOURCES = {
+    "cheb_step_kernel": ["step.cuh", "cheb.cu", "gp_internal.h", "schedule.cpp"],
+    "spmm_step_kernel": ["batch.cu", "batch.h", "gp_internal.h"],
+}
+
+
+def source_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2412_10789_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic():
     """dram bytes per launch of the step kernel from the committed ncu summary,
     or None when absent or taken on different kernel source."""
@@ -234,7 +305,6 @@ def ncu_traffic():
             prof = json.load(f)
     except (OSError, ValueError):
         return None
-    from paper_2412_10789_gb300.ncu_summary import source_hash
     if prof.get("kernel_source_hash") != source_hash(prof.get("kernel", "cheb_step_kernel")):
         return None
     return prof.get("dram_bytes_per_launch_full_size")
@@ -311,10 +381,13 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- CPU oracle leg
 
-def time_oracle(g, queries, tol, seconds):
+def time_oracle(g, queries, tol, seconds, threads=None):
     """The FP64 oracle (Algorithm 3 with the same l1 stop reading), as it stands,
-    on the host cores, on the first queries of the workload until `seconds` pass."""
+    on the host cores (all of them, or `threads`), on the first queries of the
+    workload until `seconds` pass (at least one query)."""
     import oracle as O
+    if threads is not None:
+        O.set_threads(threads)
     t0 = time.perf_counter()
     done = 0
     for fn, s, p in queries:
@@ -323,7 +396,53 @@ def time_oracle(g, queries, tol, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return done, dt, O.num_threads()
+    used = O.num_threads()
+    return done, dt, used
+
+
+def oracle_leg(g, queries, tol, seconds, captured, single_K):
+    """The CPU baseline leg: the FP64 oracle timed on all host cores and on one
+    core (bounded samples of the workload), and the oracle's converged vectors
+    y* = f(P) e_s (ChebyPower to l1 1e-12) of the sampled queries, against which
+    the sampled GPU outputs of every form are measured (l1 and max-abs).  The
+    single form is also compared element-wise with the oracle at its own K."""
+    import oracle as O
+    all_threads = O.num_threads()
+    done, dt, used = time_oracle(g, queries, tol, seconds)
+    done1, dt1, _ = time_oracle(g, queries, tol, seconds / 2, threads=1)
+    O.set_threads(all_threads)
+    cpu = {"value": done / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+           "sample": f"first {done} queries of the workload (alternating SSPPR/HKPR, l1 stop {tol:g}) "
+                     f"in {dt:.1f} s, FP64 CPU oracle, OpenMP over rows",
+           "one_thread": {"value": done1 / dt1, "unit": UNIT, "cores": 1,
+                          "sample": f"first {done1} queries in {dt1:.1f} s on one thread"}}
+    errors = {}
+    sample = sorted({i for form in captured.values() for i in form["y"]})
+    ystar = {}
+    for i in sample:
+        fn, s, p = queries[i]
+        ystar[i], _, _ = O.chebypower_tol(g, s, "ppr" if fn == 0 else "hkpr", p, 1e-12)
+    for name, form in captured.items():
+        rows = []
+        for i, y in sorted(form["y"].items()):
+            d = y - ystar[i]
+            t = form["tol"][i] if isinstance(form["tol"], dict) else form["tol"]
+            rows.append({"query": i, "l1": float(np.abs(d).sum()), "maxabs": float(np.abs(d).max()), "l1_tol": t})
+        errors[name] = {"l1_max": max(r["l1"] for r in rows), "maxabs_max": max(r["maxabs"] for r in rows),
+                        "within_tol": all(r["l1"] <= r["l1_tol"] for r in rows), "queries": rows}
+    if "single" in captured and single_K:
+        rows = []
+        for i, y in sorted(captured["single"]["y"].items()):
+            fn, s, p = queries[i]
+            want = O.chebypower(g, s, "ppr" if fn == 0 else "hkpr", p, single_K[i])
+            d = y - want
+            rows.append({"query": i, "K": single_K[i], "l1": float(np.abs(d).sum()), "maxabs": float(np.abs(d).max())})
+        errors["single"]["same_K"] = {"l1_max": max(r["l1"] for r in rows),
+                                      "maxabs_max": max(r["maxabs"] for r in rows), "bar": "l1 <= 1e-6, max-abs <= 1e-8",
+                                      "queries": rows}
+    errors["reference"] = "FP64 oracle ChebyPower to l1 1e-12 (converged y*), queries " + \
+        ", ".join(f"{i}: {'SSPPR' if queries[i][0] == 0 else 'HKPR'} s={queries[i][1]}" for i in sample)
+    return cpu, errors
 
 
 def run_reference(args, rank, world):
@@ -382,6 +501,9 @@ def run_ours(args, rank, world):
         build.build()
     dist_barrier(world)
     g, queries = workload(args.scale, args.sources)
+    forms = set(args.forms.split(","))
+    sample = list(range(min(args.cpu_sample, len(queries))))
+    captured, single_K = {}, {}
     dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree)
     ys = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range(2)]
     stream = torch.cuda.current_stream()
@@ -394,86 +516,103 @@ def run_ours(args, rank, world):
             else:
                 gp.gp_hkpr(dg, s, p, args.tol, y, info=host)
 
-    # ---- warm-up
-    for _ in range(args.warmup):
-        one_step(ys)
-    torch.cuda.synchronize()
-    # ---- timed region (device-resident outputs)
-    sampler = ClockSampler(local)
-    sampler.start()
-    gp.gp_profile_enable(dg, True)
-    gp.gp_profile_read(dg)
-    launches0 = gp.gp_launch_count()
-    dist_barrier(world)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        one_step(ys)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    dist_barrier(world)
-    launches = gp.gp_launch_count() - launches0
-    prof = gp.gp_profile_read(dg)
-    gp.gp_profile_enable(dg, False)
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms = dist_max(ms, world, dev)
-    nq = len(queries) * args.steps * world
-    value = nq / (ms / 1000.0)
-    # ---- e2e: public API, host pinned outputs, D2H inside the timed region
-    e2e = None
-    if not args.no_e2e:
-        hs = [torch.empty(g.n, dtype=torch.float64).pin_memory() for _ in range(2)]
-        one_step(hs)
+    value = ms = None
+    e2e = roofline = clocks = power = None
+    launches = 0
+    if "single" in forms:
+        # ---- warm-up
+        for _ in range(args.warmup):
+            one_step(ys)
+        torch.cuda.synchronize()
+        # ---- timed region (device-resident outputs)
+        sampler = ClockSampler(local)
+        sampler.start()
+        gp.gp_profile_enable(dg, True)
+        gp.gp_profile_read(dg)
+        launches0 = gp.gp_launch_count()
         dist_barrier(world)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
         for _ in range(args.steps):
-            one_step(hs, host=True)
+            one_step(ys)
+        ev1.record(stream)
         torch.cuda.synchronize()
-        dt = dist_max(time.perf_counter() - t0, world, dev)
-        e2e = {"value": nq / dt, "unit": UNIT,
-               "h2d_bytes_per_step": len(queries) * (4 + 8 + 8),
-               "d2h_bytes_per_step": len(queries) * g.n * 8}
-    # ---- optional GPU PwMethod baseline on the same queries
-    power = None
-    if args.power_baseline:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for fn, s, p in queries:
-            gp.gp_power(dg, fn, s, p, args.tol, ys[0], info=False)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        power = {"value": len(queries) / dt, "unit": UNIT, "what": "Algorithm 1 on the same GPU, same queries"}
+        dist_barrier(world)
+        launches = gp.gp_launch_count() - launches0
+        prof = gp.gp_profile_read(dg)
+        gp.gp_profile_enable(dg, False)
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        ms = dist_max(ms, world, dev)
+        nq = len(queries) * args.steps * world
+        value = nq / (ms / 1000.0)
+        # the sampled queries once more (the same deterministic path) into buffers of their own
+        ysamp = {i: torch.empty(g.n, dtype=torch.float64, device=dev) for i in sample}
+        for i in sample:
+            fn, s, p = queries[i]
+            single_K[i] = (gp.gp_ppr if fn == 0 else gp.gp_hkpr)(dg, s, p, args.tol, ysamp[i])["K"]
+        captured["single"] = {"tol": args.tol, "y": {i: _host(y) for i, y in ysamp.items()}}
+        del ysamp
+        # ---- e2e: public API, host pinned outputs, D2H inside the timed region
+        if not args.no_e2e:
+            hs = [torch.empty(g.n, dtype=torch.float64).pin_memory() for _ in range(2)]
+            one_step(hs)
+            dist_barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                one_step(hs, host=True)
+            torch.cuda.synchronize()
+            dt = dist_max(time.perf_counter() - t0, world, dev)
+            e2e = {"value": nq / dt, "unit": UNIT,
+                   "h2d_bytes_per_step": len(queries) * (4 + 8 + 8),
+                   "d2h_bytes_per_step": len(queries) * g.n * 8}
+        # ---- GPU PwMethod (Algorithm 1) on the same queries and GPU
+        if not args.no_power_baseline:
+            for fn, s, p in queries[:2]:
+                gp.gp_power(dg, fn, s, p, args.tol, ys[0], info=False)
+            torch.cuda.synchronize()
+            dist_barrier(world)
+            t0 = time.perf_counter()
+            Ns = []
+            for fn, s, p in queries:
+                Ns.append(gp.gp_power(dg, fn, s, p, args.tol, ys[0])["K"] + 1)
+            torch.cuda.synchronize()
+            dt = dist_max(time.perf_counter() - t0, world, dev)
+            pv = len(queries) * world / dt
+            power = {"value": pv, "unit": UNIT, "what": "Algorithm 1 (PwMethod) on the same GPU and queries, "
+                                                        "N terms by the Taylor tail <= l1 tol, same step kernel",
+                     "mean_N": float(np.mean(Ns)), "chebypower_over_pwmethod": value / pv}
+        peak, peak_kind = measured_peaks()
+        mean_launch_ms = prof["step_ms"] / max(prof["step_launches"], 1)
+        bytes_per_launch = prof["step_bytes"] / max(prof["step_launches"], 1)
+        achieved = bytes_per_launch / (mean_launch_ms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic(), "peak_kind": peak_kind,
+                    "kernel": "cheb_step_kernel (+ cheb_long_kernel, one pass)",
+                    "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_launch_ms,
+                    "launches": prof["step_launches"]}
     # ---- batched and served forms on the same graph and queries
-    forms = set(args.forms.split(","))
     batched = None
     if not args.no_batched and "batched" in forms:
-        batched = bench_batched(gp, dg, g, queries, dev, world, storages=args.batch_storage.split(","),
-                                reps=args.batch_reps, width=args.batch_width, single_value=value,
-                                single_tol=args.tol)
-    serving = None if args.no_batched or "serving" not in forms else bench_serving(gp, g, queries, dev, world)
-    # ---- CPU oracle baseline (rank 0, N = 1 only)
-    cpu = None
+        batched, outs = bench_batched(gp, dg, g, queries, dev, world, storages=args.batch_storage.split(","),
+                                      reps=args.batch_reps, width=args.batch_width, single_value=value,
+                                      single_tol=args.tol, sample=sample)
+        captured.update(outs)
+    serving = None
+    if not args.no_batched and "serving" in forms:
+        serving, outs = bench_serving(gp, g, queries, dev, world, nreq=args.serve_requests, sample=sample)
+        captured.update(outs)
+    # ---- CPU oracle baseline and the errors of every result (rank 0, N = 1 only)
+    cpu = errors = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        done, dt, threads = time_oracle(g, queries, args.tol, args.cpu_seconds)
-        cpu = {"value": done / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {done} queries of the workload (alternating SSPPR/HKPR, l1 stop {args.tol:g}) "
-                         f"in {dt:.1f} s, FP64 CPU oracle, OpenMP over rows"}
-    peak, peak_kind = measured_peaks()
-    mean_launch_ms = prof["step_ms"] / max(prof["step_launches"], 1)
-    bytes_per_launch = prof["step_bytes"] / max(prof["step_launches"], 1)
-    achieved = bytes_per_launch / (mean_launch_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(), "peak_kind": peak_kind, "kernel": "cheb_step_kernel (+ cheb_long_kernel, one pass)",
-                "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_launch_ms,
-                "launches": prof["step_launches"]}
+        cpu, errors = oracle_leg(g, queries, args.tol, args.cpu_seconds, captured, single_K)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps if ms else None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(g, args, per_step_queries=len(queries)),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clocks,
@@ -484,6 +623,8 @@ def run_ours(args, rank, world):
             out["batched"] = batched
         if serving:
             out["serving"] = serving
+        if errors:
+            out["errors_vs_oracle"] = errors
         print(json.dumps(out), flush=True)
     dg.close()
     if world > 1:
@@ -530,9 +671,11 @@ def batched_forms(gp, g, queries, forms, width, reps, dev):
 
 
 def serve_poisson(gp, g, dev, args):
-    """gp_submit/gp_poll under Poisson arrivals: the saturated rate first (all
-    requests at once), then each offered load as a fraction of it; latency is
-    arrival to completion (the service's own clock), per request."""
+    """gp_submit/gp_poll under Poisson arrivals on the Chung-Lu graph: the
+    saturated rate first (all requests at once), then each offered load as a
+    fraction of it; latency is arrival to completion (the service's own clock),
+    per request.  Mixed SSPPR/HKPR with alpha in {0.1, 0.2, 0.5}, t in
+    {3, 5, 10}, l1 tolerance drawn from {1e-4, 1e-5, 1e-6}."""
     import torch
     rng = np.random.default_rng(5)
     nreq = args.requests
@@ -540,42 +683,10 @@ def serve_poisson(gp, g, dev, args):
     fns = rng.integers(0, 2, nreq)
     params = [(0.1, 0.2, 0.5)[k] if f == 0 else (3.0, 5.0, 10.0)[k] for f, k in zip(fns, rng.integers(0, 3, nreq))]
     tols = rng.choice([1e-4, 1e-5, 1e-6], nreq)
+    specs = [(int(f), int(s), float(p), float(t)) for f, s, p, t in zip(fns, srcs, params, tols)]
     dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=args.serve_width)
     pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range(args.serve_width + 64)]
-    free = list(range(len(pool)))
-
-    def run(arrivals):
-        """Submit request i at arrivals[i] (seconds from start); returns (wall, latencies)."""
-        pending = {}
-        lat = []
-        t0 = time.perf_counter()
-        i = 0
-        while i < nreq or pending:
-            now = time.perf_counter() - t0
-            while i < nreq and arrivals[i] <= now and free:
-                b = free.pop()
-                r = gp.make_request(int(fns[i]), int(srcs[i]), float(params[i]), float(tols[i]), pool[b])
-                pending[gp.gp_submit(dg, r)] = b
-                i += 1
-            for tk in list(pending):
-                inf = gp.gp_poll(dg, tk)
-                if inf is not None:
-                    lat.append(inf["ms"])
-                    free.append(pending.pop(tk))
-            time.sleep(0.0002)
-        return time.perf_counter() - t0, lat
-
-    wall, lat = run(np.zeros(nreq))
-    sat = nreq / wall
-    res = {"saturated": {"value": sat, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99))}}
-    for load in [float(x) for x in args.loads.split(",")]:
-        gaps = rng.exponential(1.0 / (load * sat), nreq)
-        wall, lat = run(np.cumsum(gaps))
-        res[f"load_{load:g}"] = {"offered": load * sat, "value": nreq / wall, "unit": UNIT,
-                                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
-    stats = gp.gp_serve_stats(dg)
-    res["mean_active_columns"] = stats["mean_active"]
+    res, _ = serve_levels(gp, dg, specs, pool, [float(x) for x in args.loads.split(",")], 5)
     dg.close()
     return res
 

@@ -168,6 +168,20 @@ def from_edges(n: int, edges, name: str = "edges") -> Graph:
     return Graph(name, n, rp, ci)
 
 
+def complete(n: int) -> Graph:
+    """The complete graph K_n (every pair of distinct nodes, both directions):
+    n (n - 1) entries, so n >= 46342 passes 2^31 entries (int64 row offsets)."""
+    rp = np.arange(n + 1, dtype=np.int64) * (n - 1)
+    ci = np.empty(n * (n - 1), dtype=np.int32)
+    j = np.arange(n - 1, dtype=np.int32)[None, :]
+    step = max(1, (1 << 26) // max(n, 1))
+    for u0 in range(0, n, step):
+        u1 = min(n, u0 + step)
+        u = np.arange(u0, u1, dtype=np.int32)[:, None]
+        ci[u0 * (n - 1):u1 * (n - 1)] = (j + (j >= u)).ravel()  # row u: 0..u-1, u+1..n-1
+    return Graph(f"complete_n{n}", n, rp, ci)
+
+
 def sources(g: Graph, k: int, seed: int) -> np.ndarray:
     """k distinct sources drawn uniformly among nodes with degree >= 1."""
     lib = _load()

@@ -51,7 +51,7 @@ typedef enum {
   GP_ECUDA = 3,      /* a CUDA call failed (message in gp_last_error) */
   GP_EAGAIN = 4,     /* gp_poll: the query is not finished yet */
   GP_ENOTFOUND = 5,  /* gp_poll: unknown ticket */
-  GP_ETIMEDOUT = 6,  /* a bounded device-side wait ran out */
+  GP_ETIMEDOUT = 6,  /* gp_wait: the ticket did not complete within the timeout */
   GP_EBUSY = 7,      /* the serving queue is full */
   GP_ENOTSUP = 8     /* a combination of options this build does not support */
 } gp_status;
@@ -290,6 +290,13 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
 gp_status gp_submit(gp_graph* g, const gp_request* req, uint64_t* ticket);
 gp_status gp_poll(gp_graph* g, uint64_t ticket, gp_query_info* info);
 
+/* Block until the ticket completes (then as gp_poll: GP_OK with info, or the
+ * service's error), for at most timeout_ms milliseconds of host time: a bounded
+ * host-side wait that returns GP_ETIMEDOUT when the time runs out (the ticket
+ * stays queued or in flight and can be waited for again).  GP_ENOTFOUND for an
+ * unknown or already-collected ticket; timeout_ms must be >= 0. */
+gp_status gp_wait(gp_graph* g, uint64_t ticket, double timeout_ms, gp_query_info* info);
+
 /* Serving statistics since the graph was created: completed queries, steps
  * run (one fused pass over each block half that has active columns), and the
  * mean number of active columns per step. */
@@ -301,15 +308,22 @@ gp_status gp_serve_stats(gp_graph* g, uint64_t* completed, uint64_t* steps, doub
  * they query: a host framework that owns all device memory, or a loop that
  * cannot afford cudaFree's device-wide synchronisation or a failing
  * cudaMalloc).  It runs the Chebyshev recurrence for exactly K steps on the
- * caller's CSR (device pointers, int32 row_ptr and col_idx, natural order, the
- * rules of gp_graph_create; not validated here) and writes n doubles to the
- * device buffer y_out, on `stream` (cudaStream_t, NULL = default stream),
- * stream-ordered.  Its scratch is one 16 MiB array in device memory that every
- * GPU loading this library holds until the process exits, so n must be
- * <= 1,048,576 (GP_EINVAL otherwise); 1 <= K <= 256; t <= 1000.  All calls on a
- * device share that array: calls that overlap on the GPU race and corrupt each
- * other.  The first call on a device looks up the array's address and should
- * come before any stream capture.
+ * caller's CSR (device pointers, int32 row_ptr and col_idx, natural order)
+ * and writes n doubles to the device buffer y_out, on `stream` (cudaStream_t,
+ * NULL = default stream), stream-ordered: every call only enqueues kernels
+ * (the source's degree is read on the device), so it returns without waiting
+ * for the GPU.  The CSR is not validated here; it must satisfy what
+ * gp_graph_create checks: sorted rows without duplicates or self-loops and
+ * both directions of every edge (an undirected graph, Section 2.1).  A row may
+ * list a node whose own row is empty; that node contributes nothing
+ * (1/d := 0).  An isolated source gives f(0) e_s.  Its scratch is one 16 MiB
+ * array in device memory that every GPU loading this library holds until the
+ * process exits, so n must be <= 1,048,576 (GP_EINVAL otherwise);
+ * 1 <= K <= 256; t <= 1000.  All calls on a device share that array: calls that
+ * overlap on the GPU race and corrupt each other.  The first call on a device
+ * looks up the array's address, keeps it for the life of the process, and
+ * should come before any stream capture; do not call it on a device after
+ * cudaDeviceReset.
  */
 gp_status gp_query_static(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                           int32_t function, int32_t source, double param, int32_t K, double* y_out,

@@ -146,6 +146,16 @@ extern "C" gp_status gp_poll(gp_graph* gh, uint64_t ticket, gp_query_info* info)
   return rc != GP_OK ? rc : st;
 }
 
+extern "C" gp_status gp_wait(gp_graph* gh, uint64_t ticket, double timeout_ms, gp_query_info* info) {
+  gp_status st = GP_OK;
+  gp_status rc = guard([&] {
+    Graph* g = as_graph(gh);
+    GP_REQUIRE(timeout_ms >= 0.0, "timeout_ms must be >= 0");
+    st = serve_wait(*g, ticket, timeout_ms, info);
+  });
+  return rc != GP_OK ? rc : st;
+}
+
 extern "C" gp_status gp_batch_clenshaw(gp_graph* gh, int32_t count, const gp_request* reqs, gp_query_info* infos) {
   return guard([&] {
     Graph* g = as_graph(gh);

@@ -44,8 +44,9 @@ __host__ __device__ inline float2 split_df(double x) {
   return make_float2(hi, lo);
 }
 
-// r_0 = e_s, r_1 = P e_s: Q_0(s) = 1/d_s; for v in N(s), r_1(v) = 1/d_s and
-// Q_1(v) = 1/(d_s d_v); y = c_0 r_0 + c_1 r_1.  (Algorithm 3, first line.)
+// r_0 = e_s, r_1 = P e_s: Q_0(s) = 1/d_s; for v in N(s) with d_v > 0,
+// r_1(v) = 1/d_s and Q_1(v) = 1/(d_s d_v); y = c_0 r_0 + c_1 r_1.  (Algorithm 3,
+// first line.)
 template <typename RP>
 __global__ void cheb_init_kernel(const __grid_constant__ InitArgs a) {
   const RP* rp = (const RP*)a.rp;
@@ -61,6 +62,9 @@ __global__ void cheb_init_kernel(const __grid_constant__ InitArgs a) {
   }
   for (int64_t e = beg + tid; e < end; e += (int64_t)gridDim.x * blockDim.x) {
     int32_t v = a.ci[e];
+    // a listed node with an empty row (only an unvalidated asymmetric CSR has
+    // one) has (P e_s)(v) = 0: its own row gathers nothing
+    if (rp[v + 1] == rp[v]) continue;
     double dv = (double)(rp[v + 1] - rp[v]);
     a.q1[v] = (float)(1.0 / (ds * dv));
     if (a.cheb) a.y[v] = split_df(a.c1 / ds);

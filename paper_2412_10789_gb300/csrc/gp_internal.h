@@ -54,6 +54,11 @@ inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_o
 // tail[k] = sum_{l>k} |c_l| (the sum continues past kmax until negligible).
 void cheb_coefficients(int function, double param, int kmax, std::vector<double>& c,
                        std::vector<double>& tail);
+// The same c_0..c_kmax written into c[kmax + 1] without allocating: the HKPR
+// recurrence uses `work` (cheb_coefficients_work(...) doubles at least;
+// returns false when work_len is smaller).
+int cheb_coefficients_work(int function, double param, int kmax);
+bool cheb_coefficients_into(int function, double param, int kmax, double* c, double* work, int work_len);
 // Taylor coefficients zeta_0..zeta_{N-1} (Def. SSPPR / Def. HKPR) with
 // N = smallest count whose tail sum_{k>=N} zeta_k <= tol (capped at nmax).
 void taylor_coefficients(int function, double param, double tol, int nmax, std::vector<double>& z);
@@ -229,6 +234,7 @@ TunedBlock tune_block(Graph& g, gp_dtype storage, std::vector<int> widths);
 void free_batch_work(Graph& g);
 uint64_t serve_submit(Graph& g, const gp_request& req);
 gp_status serve_poll(Graph& g, uint64_t ticket, gp_query_info* info);
+gp_status serve_wait(Graph& g, uint64_t ticket, double timeout_ms, gp_query_info* info);
 void serve_stats(Graph& g, uint64_t* completed, uint64_t* steps, double* mean_active);
 void serve_shutdown(Graph& g);
 

@@ -18,7 +18,17 @@
 // whose work overlaps on the GPU (different streams, or different host threads)
 // race on the array and corrupt each other's results.  The first call on a
 // device looks up the array's device address (cudaGetSymbolAddress, with that
-// device current); that first call should come before any stream capture.
+// device current) and keeps it for the life of the process; that first call
+// should come before any stream capture, and the entry point must not be used
+// on a device after cudaDeviceReset (the kept address would be stale).  Every
+// later call only enqueues kernels: the source's degree is read on the device,
+// so no call waits for the GPU.
+//
+// The CSR is the caller's and is not checked here: sorted rows without
+// duplicates or self-loops, both directions of every edge (Section 2.1), the
+// conditions gp_graph_create validates.  A row may list a node whose own row
+// is empty; that node contributes nothing (1/d := 0, the reading of P's
+// degree-0 columns the rest of the library uses).
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -28,6 +38,9 @@
 constexpr int64_t kStaticMaxN = int64_t(1) << 20;
 constexpr int kStaticMaxK = 256;
 constexpr int kStaticMaxDevices = 64;
+constexpr double kStaticMaxT = 1000.0;
+// Work array of the HKPR coefficient recurrence for t <= kStaticMaxT, K <= kStaticMaxK.
+constexpr int kStaticCoeffWork = 4096;
 // Q_a, Q_b (n floats each) and y (n float pairs): 16 MiB.
 constexpr size_t kStaticBytes = (size_t)kStaticMaxN * (4 + 4 + 8);
 
@@ -50,37 +63,6 @@ void* static_scratch(int dev) {
   return g_static_addr[dev];
 }
 
-// c_0..c_K of Lemma 2 (SSPPR) or Lemma 3 (HKPR, by Miller's backward
-// recurrence normalised with I_0 + 2 sum_k I_k = e^t), in fixed arrays.
-void static_coefficients(int function, double param, int K, double* c) {
-  if (function == GP_FN_PPR) {
-    const double root = std::sqrt(param * (2.0 - param));
-    const double gamma = param / root, beta = (1.0 - param) / (1.0 + root);
-    double p = 1.0;
-    c[0] = gamma;
-    for (int k = 1; k <= K; ++k) {
-      p *= beta;
-      c[k] = 2.0 * gamma * p;
-    }
-    return;
-  }
-  constexpr int kTop = 2048;
-  double v[kTop + 2];
-  int top = (int)std::ceil(param + 12.0 * std::sqrt(param) + 40.0) + K + 24;
-  if (top > kTop) top = kTop;
-  v[top + 1] = 0.0;
-  v[top] = 1e-280;
-  for (int k = top; k >= 1; --k) {
-    v[k - 1] = (2.0 * k / param) * v[k] + v[k + 1];
-    if (v[k - 1] > 1e250)
-      for (int j = k - 1; j <= top; ++j) v[j] *= 1e-250;
-  }
-  double norm = v[0];
-  for (int k = 1; k <= top; ++k) norm += 2.0 * v[k];
-  c[0] = v[0] / norm;
-  for (int k = 1; k <= K; ++k) c[k] = 2.0 * v[k] / norm;
-}
-
 __global__ void static_zero_kernel(int64_t n, float* qa, float* qb, float2* y) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
     qa[u] = 0.f;
@@ -95,10 +77,12 @@ __host__ __device__ inline float2 static_split(double x) {
 }
 
 // r_0 = e_s (Q_0(s) = 1/d_s), r_1 = P e_s (Q_1(v) = 1/(d_s d_v) for v in N(s)),
-// y = c_0 r_0 + c_1 r_1.
+// y = c_0 r_0 + c_1 r_1.  An isolated source writes nothing (the output kernel
+// answers f(0) e_s); a listed neighbour with an empty row keeps r_1(v) = 0.
 __global__ void static_init_kernel(const int32_t* rp, const int32_t* ci, int64_t s, double c0, double c1,
                                    float* q0, float* q1, float2* y) {
   const int64_t beg = rp[s], end = rp[s + 1];
+  if (beg == end) return;
   const double ds = (double)(end - beg);
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid == 0) {
@@ -107,7 +91,9 @@ __global__ void static_init_kernel(const int32_t* rp, const int32_t* ci, int64_t
   }
   for (int64_t e = beg + tid; e < end; e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = ci[e];
-    q1[v] = (float)(1.0 / (ds * (double)(rp[v + 1] - rp[v])));
+    const int32_t dv = rp[v + 1] - rp[v];
+    if (dv == 0) continue;
+    q1[v] = (float)(1.0 / (ds * (double)dv));
     y[v] = static_split(c1 / ds);
   }
 }
@@ -143,7 +129,10 @@ __global__ void static_step_kernel(int64_t n, const int32_t* rp, const int32_t* 
   }
 }
 
-__global__ void static_out_kernel(int64_t n, const float2* y, int64_t s, int isolated, double f0, double* out) {
+// y_out = y as doubles; for an isolated source (read from row_ptr here) f(0) e_s.
+__global__ void static_out_kernel(int64_t n, const int32_t* rp, const float2* y, int64_t s, double f0,
+                                  double* out) {
+  const bool isolated = rp[s] == rp[s + 1];
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
     out[u] = isolated ? (u == s ? f0 : 0.0) : (double)y[u].x + (double)y[u].y;
 }
@@ -168,7 +157,7 @@ extern "C" gp_status gp_query_static(int64_t n, int64_t nnz, const int32_t* row_
     if (function == GP_FN_PPR)
       GP_REQUIRE(param > 0.0 && param < 1.0, "alpha must be in (0, 1)");
     else
-      GP_REQUIRE(param > 0.0 && param <= 1000.0, "t must be in (0, 1000]");
+      GP_REQUIRE(param > 0.0 && param <= kStaticMaxT, "t must be in (0, 1000]");
     GP_REQUIRE(K >= 1 && K <= kStaticMaxK, "K must be in [1, 256]");
     int dev = 0;
     GP_CUDA_TRY(cudaGetDevice(&dev));
@@ -178,23 +167,19 @@ extern "C" gp_status gp_query_static(int64_t n, int64_t nnz, const int32_t* row_
     float* qb = qa + kStaticMaxN;
     float2* y = (float2*)(qb + kStaticMaxN);
     cudaStream_t st = (cudaStream_t)stream;
-    int32_t rs[2];
-    GP_CUDA_TRY(cudaMemcpyAsync(rs, row_ptr + source, sizeof(rs), cudaMemcpyDeviceToHost, st));
-    GP_CUDA_TRY(cudaStreamSynchronize(st));
-    const int64_t ds = (int64_t)rs[1] - rs[0];
     int sms = 0;
     GP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (ds == 0) {  // isolated source: y = f(0) e_s
-      const double f0 = function == GP_FN_PPR ? param : std::exp(-param);
-      static_out_kernel<<<sms * 4, 256, 0, st>>>(n, y, source, 1, f0, y_out);
-      GP_LAUNCHED();
-      return;
-    }
-    double c[kStaticMaxK + 1];
-    static_coefficients(function, param, K, c);
+    // c_0..c_K (Lemma 2 / Lemma 3) from the library's coefficient engine, in
+    // fixed arrays on the host stack
+    double c[kStaticMaxK + 2];
+    double work[kStaticCoeffWork];
+    if (!cheb_coefficients_into(function, param, K + 1, c, work, kStaticCoeffWork))
+      throw Error{GP_EINVAL, "gp_query_static: t too large for the fixed coefficient work array"};
+    const double f0 = function == GP_FN_PPR ? param : std::exp(-param);
     static_zero_kernel<<<sms * 4, 256, 0, st>>>(n, qa, qb, y);
     GP_LAUNCHED();
-    const int init_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((ds + 255) / 256, sms * 4));
+    // the source row has at most n - 1 entries; blocks past its end return at once
+    const int init_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sms * 4));
     static_init_kernel<<<init_blocks, 256, 0, st>>>(row_ptr, col_idx, source, c[0], c[1], qa, qb, y);
     GP_LAUNCHED();
     float* bufs[2] = {qa, qb};  // bufs[k & 1] holds Q_k
@@ -204,7 +189,7 @@ extern "C" gp_status gp_query_static(int64_t n, int64_t nnz, const int32_t* row_
                                                   ck.y);
       GP_LAUNCHED();
     }
-    static_out_kernel<<<sms * 4, 256, 0, st>>>(n, y, source, 0, 0.0, y_out);
+    static_out_kernel<<<sms * 4, 256, 0, st>>>(n, row_ptr, y, source, f0, y_out);
     GP_LAUNCHED();
   });
 }

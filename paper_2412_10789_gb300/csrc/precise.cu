@@ -46,6 +46,7 @@ __global__ void precise_init_kernel(const RP* rp, const int32_t* ci, int64_t s, 
   for (int64_t e = beg + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < end;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = ci[e];
+    if (rp[v + 1] == rp[v]) continue;  // a listed node without neighbours: (P e_s)(v) = 0
     q1[v] = pair_of(1.0 / (ds * (double)(rp[v + 1] - rp[v])));
     if (cheb) y[v] = pair_of(c1 / ds);
   }

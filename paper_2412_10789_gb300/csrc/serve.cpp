@@ -250,6 +250,42 @@ gp_status serve_poll(Graph& g, uint64_t ticket, gp_query_info* info) {
   return GP_ENOTFOUND;
 }
 
+gp_status serve_wait(Graph& g, uint64_t ticket, double timeout_ms, gp_query_info* info) {
+  Serve* s = static_cast<Serve*>(g.serve);
+  if (!s) {
+    set_last_error("unknown ticket");
+    return GP_ENOTFOUND;
+  }
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                            std::chrono::duration<double, std::milli>(std::max(0.0, timeout_ms)));
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    auto it = s->done.find(ticket);
+    if (it != s->done.end()) {
+      const Done d = it->second;
+      s->done.erase(it);
+      if (d.status != GP_OK) {
+        set_last_error(s->error);
+        return d.status;
+      }
+      if (info) *info = d.info;
+      return GP_OK;
+    }
+    bool known = s->inflight.count(ticket) > 0;
+    for (const Ticket& t : s->pending) known = known || t.id == ticket;
+    if (!known) {
+      set_last_error("unknown ticket");
+      return GP_ENOTFOUND;
+    }
+    // finish() and fail() notify the condition variable; wake at the deadline otherwise
+    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout && !s->done.count(ticket)) {
+      set_last_error("gp_wait: the ticket did not complete within " + std::to_string(timeout_ms) + " ms");
+      return GP_ETIMEDOUT;
+    }
+  }
+}
+
 void serve_stats(Graph& g, uint64_t* completed, uint64_t* steps, double* mean_active) {
   Serve* s = static_cast<Serve*>(g.serve);
   uint64_t c = 0, p = 0;

@@ -6,7 +6,7 @@ Every computation runs in ``libgpcheby.so``.  PyTorch supplies device memory
 compiled library is missing; there is no fallback.
 
 The functions keep the C names: ``gp_graph_create``, ``gp_ppr``, ``gp_hkpr``,
-``gp_query``, ``gp_power``, ``gp_batch``, ``gp_submit``, ``gp_poll``,
+``gp_query``, ``gp_power``, ``gp_batch``, ``gp_submit``, ``gp_poll``, ``gp_wait``,
 ``gp_graph_destroy`` and the helpers.  Vectors are torch tensors (CUDA tensors
 for device buffers, CPU tensors -- ideally pinned -- for host buffers) or
 numpy arrays for host inputs.
@@ -126,6 +126,7 @@ def load_library():
                                                     ctypes.c_int, pinfo]),
             "gp_submit": (ctypes.c_int, [vp, ctypes.POINTER(gp_request), ctypes.POINTER(u64)]),
             "gp_poll": (ctypes.c_int, [vp, u64, pinfo]),
+            "gp_wait": (ctypes.c_int, [vp, u64, dbl, pinfo]),
             "gp_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                               ctypes.POINTER(dbl)]),
             "gp_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(i32), i32, ctypes.POINTER(i32),
@@ -401,6 +402,14 @@ def gp_poll(g: Graph, ticket: int):
     if rc == GP_EAGAIN:
         return None
     _check(rc)
+    return inf.as_dict()
+
+
+def gp_wait(g: Graph, ticket: int, timeout_ms: float):
+    """Block until the ticket completes (info dict) or timeout_ms passes
+    (GPError with GP_ETIMEDOUT); other errors raise as well."""
+    inf = gp_query_info()
+    _check(_lib.gp_wait(g.handle, ctypes.c_uint64(ticket), float(timeout_ms), ctypes.byref(inf)))
     return inf.as_dict()
 
 

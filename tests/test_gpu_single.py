@@ -342,3 +342,40 @@ def graph_rmat22():
     if "rmat22" not in _G:
         _G["rmat22"] = gg.rmat(22, 16, seed=2)
     return _G["rmat22"]
+
+
+def _with_isolated_targets(scale, extra_rows):
+    """An R-MAT CSR whose first `extra_rows` non-empty rows also list a node
+    with an empty row (asymmetric; accepted with the symmetry check off)."""
+    base = gg.rmat(scale, 8, seed=5)
+    rows = [list(base.col_idx[base.row_ptr[u]:base.row_ptr[u + 1]]) for u in range(base.n)]
+    iso = [u for u in range(base.n) if not rows[u]]
+    assert len(iso) >= 3
+    for k, u in enumerate([u for u in range(base.n) if rows[u]][:extra_rows]):
+        rows[u] = sorted(set(rows[u]) | {iso[k % len(iso)]})
+    rp = np.zeros(base.n + 1, dtype=np.int64)
+    for u in range(base.n):
+        rp[u + 1] = rp[u] + len(rows[u])
+    ci = np.array([v for r in rows for v in r], dtype=np.int32)
+    return gg.Graph(f"rmat{scale}_with_isolated_targets", base.n, rp, ci)
+
+
+@pytest.mark.parametrize("precise_rows", [0, -1])
+def test_unvalidated_asymmetric_csr(gp, precise_rows):
+    """Rows that list nodes with empty rows: those nodes contribute nothing
+    (1/d := 0) and their result entries stay 0, as in the oracle's pull form of
+    P; sources whose own row lists such a node included.  precise_rows 0 runs
+    the float-pair path on this small graph, -1 the FP32 step kernel."""
+    g = _with_isolated_targets(11, 60)
+    dg = make(gp, g, validate_symmetry=0, precise_rows=precise_rows)
+    try:
+        srcs = [u for u in range(g.n) if g.degree[u] > 0][:4]
+        for kind, param, K in (("ppr", 0.2, 20), ("hkpr", 5.0, 14)):
+            for s in srcs:
+                got, info = run(gp, dg, g, kind, s, param, K=K)
+                want = O.chebypower(g, s, kind, param, K)
+                e = O.errors(g, want, got)
+                assert np.isfinite(got).all()
+                assert e["l1"] <= L1_BAR and e["maxabs"] <= MAX_BAR, (kind, s, e)
+    finally:
+        dg.close()

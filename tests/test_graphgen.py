@@ -76,3 +76,11 @@ def test_from_edges():
     g = gg.from_edges(4, [(0, 1), (1, 0), (2, 2), (1, 3)])
     _check_simple_undirected(g)
     assert g.nnz == 4
+
+
+def test_complete_graph_csr():
+    g = gg.complete(7)
+    assert g.nnz == 42 and (g.degree == 6).all()
+    for u in range(7):
+        row = g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]]
+        assert list(row) == [v for v in range(7) if v != u]

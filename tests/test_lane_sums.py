@@ -7,12 +7,31 @@ uses (blocks of 16 entries, each block added to the running sum); the
 chunks' partials are then added in chunk order, and r, Q and y stay FP32 as
 on the device.  No GPU and no library code: the oracle and numpy only.
 """
+import os
+import re
+
 import numpy as np
 
 import graphgen as gg
 import oracle as O
 
 F32 = np.float32
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _kernel_constants():
+    """The block length of the two-level sums (kBlk) and the chunk length of a
+    long row (kBTileCap) as the batched kernel's source defines them, so the
+    emulation follows the device code if either changes."""
+    with open(os.path.join(ROOT, "paper_2412_10789_gb300", "csrc", "batch.cu")) as f:
+        src = f.read()
+    blk = int(re.search(r"constexpr int kBlk = (\d+);", src).group(1))
+    span = int(re.search(r"#define GP_SPMM_TILE (\d+)", src).group(1))
+    cap = span - int(re.search(r"constexpr int kBTileCap = kBTileSpan - (\d+);", src).group(1))
+    return blk, cap
+
+
+BLK, CHUNK = _kernel_constants()
 
 
 def _seq(x):
@@ -22,7 +41,7 @@ def _seq(x):
 def _lane(x, two_level):
     if not two_level:
         return _seq(x)
-    return _seq(np.array([_seq(x[i:i + 16]) for i in range(0, x.size, 16)], np.float32))
+    return _seq(np.array([_seq(x[i:i + BLK]) for i in range(0, x.size, BLK)], np.float32))
 
 
 def _run(g, s, kind, param, two_level):
@@ -36,7 +55,7 @@ def _run(g, s, kind, param, two_level):
         v = q[ci]
         for u in rows:
             a, b = rp[u], rp[u + 1]
-            parts = [_lane(v[c0:min(b, c0 + 508)], two_level) for c0 in range(a, b, 508)]
+            parts = [_lane(v[c0:min(b, c0 + CHUNK)], two_level) for c0 in range(a, b, CHUNK)]
             out[u] = _seq(np.array(parts, np.float32))
         return out
 
@@ -57,6 +76,7 @@ def _run(g, s, kind, param, two_level):
 
 
 def test_two_level_lane_sums_beat_sequential_ones():
+    assert (BLK, CHUNK) == (16, 508), "the kernel's sums changed: re-derive the bars below"
     g = gg.rmat(13, 16, seed=2)  # hubs of up to 2212 entries: several chunks
     seq, two = [], []
     for s in gg.sources(g, 3, 3):
