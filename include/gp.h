@@ -179,8 +179,11 @@ gp_status gp_power(gp_graph* g, int32_t function, int32_t source, double param, 
  * block and advanced together by a fused SpMM step (B = cfg.block_width or the
  * tuned width; more requests run as successive blocks).  Each column keeps its
  * own function, parameter, coefficients and K, and is retired when its own stop
- * rule fires.  T_k storage follows cfg.storage.  infos may be NULL, else it
- * receives `count` reports.
+ * rule fires.  T_k storage follows cfg.storage.  The columns accumulate the
+ * SpMM and y in FP32, so an l1 error much below 1e-6 is out of their reach
+ * (y alone is rounded once per step); smaller tolerances are accepted but
+ * only the single-query calls (float-pair y) deliver them.  infos may be NULL,
+ * else it receives `count` reports.
  */
 gp_status gp_batch(gp_graph* g, int32_t count, const gp_request* reqs, gp_query_info* infos);
 

@@ -167,7 +167,7 @@ def test_wait_times_out_then_completes(gp):
     try:
         y = torch.empty(g.n, dtype=torch.float64, device="cuda")
         s = int(gg.sources(g, 1, 4)[0])
-        t = gp.gp_submit(dg, gp.make_request(0, s, 0.1, 1e-8, y))
+        t = gp.gp_submit(dg, gp.make_request(0, s, 0.1, 1e-6, y))
         with pytest.raises(gp.GPError) as ei:
             gp.gp_wait(dg, t, 0.0)
         assert ei.value.status == gp.GP_ETIMEDOUT
@@ -175,7 +175,7 @@ def test_wait_times_out_then_completes(gp):
         info = gp.gp_wait(dg, t, 60000.0)
         assert time.perf_counter() - t0 < 60.0 and info["K"] > 0
         e = O.errors(g, O.chebypower(g, s, "ppr", 0.1, 200), y.cpu().numpy())
-        assert e["l1"] <= 1e-8
+        assert e["l1"] <= 1e-6
         with pytest.raises(gp.GPError) as ei:  # collected
             gp.gp_wait(dg, t, 10.0)
         assert ei.value.status == gp.GP_ENOTFOUND
