@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--forms", default="single,batched,serving",
                    help="comma list of the forms to time (without 'single' only the named forms run, for "
                         "profiling; the line's value is then null)")
-    p.add_argument("--serve-requests", type=int, default=512,
+    p.add_argument("--serve-requests", type=int, default=1024,
                    help="rmat22 serving leg: requests per arrival pattern")
     p.add_argument("--cpu-sample", type=int, default=4,
                    help="queries whose GPU outputs are checked against the converged FP64 oracle")
@@ -219,22 +219,26 @@ def serve_levels(gp, dg, specs, pool, loads, seed, keep=()):
     return res, kept
 
 
-def bench_serving(gp, g, queries, dev, world, nreq=512, loads=(0.5, 0.8, 0.95), sample=()):
+def bench_serving(gp, g, queries, dev, world, nreq=1024, loads=(0.5, 0.8, 0.95), sample=(), storage="fp32",
+                  tols=(1e-4, 1e-5, 1e-6), name="serving"):
     """The step's queries through gp_submit/gp_poll (continuous batching), l1
-    tolerances cycling over 1e-4, 1e-5, 1e-6: the saturated rate, then Poisson
-    arrivals at 50/80/95% of it, with p50/p99 latency (arrival to completion)."""
+    tolerances cycling over `tols`: the saturated rate, then Poisson arrivals
+    at 50/80/95% of it, with p50/p99 latency (arrival to completion).  With
+    16-bit storage the service starts each column in FP32 and moves it to a
+    16-bit block after its own warm-up."""
     import torch
     width = 256
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=width)
-    tols = [1e-4, 1e-5, 1e-6]
-    specs = [queries[i % len(queries)] + (tols[i % 3],) for i in range(nreq)]
+    st = {"fp32": gp.GP_F32, "bf16": gp.GP_BF16, "fp16": gp.GP_F16}[storage]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=width, storage=st)
+    specs = [queries[i % len(queries)] + (tols[i % len(tols)],) for i in range(nreq)]
     pool = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range(width + 64)]
     dist_barrier(world)
     res, kept = serve_levels(gp, dg, specs, pool, loads, 7, keep=sample)
     dg.close()
-    res.update({"storage": "fp32", "block_width": width, "workload": "the step's queries, tolerances 1e-4/1e-5/1e-6",
+    res.update({"storage": storage, "block_width": width,
+                "workload": "the step's queries, tolerances " + "/".join(f"{t:g}" for t in tols),
                 "arrivals": "saturated: all at once; load_x: Poisson at x times the saturated rate"})
-    outs = {"serving": {"tol": {i: specs[i][3] for i in sample}, "y": {i: _host(kept[i]) for i in sample}}}
+    outs = {name: {"tol": {i: specs[i][3] for i in sample}, "y": {i: _host(kept[i]) for i in sample}}}
     return res, outs
 
 
@@ -600,10 +604,19 @@ def run_ours(args, rank, world):
                                       reps=args.batch_reps, width=args.batch_width, single_value=value,
                                       single_tol=args.tol, sample=sample)
         captured.update(outs)
-    serving = None
+    serving = {}
     if not args.no_batched and "serving" in forms:
-        serving, outs = bench_serving(gp, g, queries, dev, world, nreq=args.serve_requests, sample=sample)
-        captured.update(outs)
+        for name, storage, tols in (("serving", "fp32", (1e-4, 1e-5, 1e-6)),
+                                    ("serving_bf16", "bf16", (1e-4, 1e-5, 1e-6)),
+                                    ("serving_bf16_tol1e-4", "bf16", (1e-4,))):
+            serving[name], outs = bench_serving(gp, g, queries, dev, world, nreq=args.serve_requests, sample=sample,
+                                                storage=storage, tols=tols, name=name)
+            captured.update(outs)
+        single4 = (batched or {}).get("bf16_tol1e-4", {}).get("single_source_same_tol")
+        if single4:
+            serving["serving_bf16_tol1e-4"]["single_source_same_tol"] = single4
+            serving["serving_bf16_tol1e-4"]["vs_single_source_same_tol"] = \
+                serving["serving_bf16_tol1e-4"]["saturated"]["value"] / single4
     # ---- CPU oracle baseline and the errors of every result (rank 0, N = 1 only)
     cpu = errors = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -621,8 +634,8 @@ def run_ours(args, rank, world):
             out["gpu_power_baseline"] = power
         if batched:
             out["batched"] = batched
-        if serving:
-            out["serving"] = serving
+        for name, res in serving.items():
+            out[name] = res
         if errors:
             out["errors_vs_oracle"] = errors
         print(json.dumps(out), flush=True)

@@ -84,7 +84,9 @@ typedef struct {
                               keep T_k as float pairs (~48 bits) instead of FP32: FP32 rounding
                               is not damped on tiny graphs with unit-modulus eigenvalues
                               (0: default 1024; -1: never) */
-  double warmup_tail;      /* 16-bit storage only once sum_m (m+1)|c_{k+1+m}| < warmup_tail (default 1e-2) */
+  double warmup_tail;      /* a column stores Q in 16 bits only once sum_m (m+1)|c_{k+1+m}| is below
+                              warmup_tail (default 1e-2) for BF16, 4 * warmup_tail for FP16, each times
+                              min(1, l1_tol / 1e-4) for the column's own tolerance */
   size_t mem_budget;       /* bytes the serving loop may use for column blocks (0: 80% of free) */
   void* (*alloc)(size_t bytes, void* ctx); /* device allocator; NULL: cudaMalloc */
   void (*free)(void* ptr, void* ctx);      /* its release function */
@@ -285,8 +287,12 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
  * block has as many slots as the memory budget allows (cfg.mem_budget, default
  * 80% of the free device memory), at most cfg.block_width (0: 256; 512 at most),
  * a power of two; a block wider than 256 columns runs as 256-column halves,
- * each with its own pass.  The request's y_out must stay valid until gp_poll reports
- * completion.
+ * each with its own pass.  With cfg.storage GP_BF16 or GP_F16 a second block of
+ * the same width stores 16 bits: every request starts in the FP32 block and
+ * moves to the 16-bit block once its own warm-up is over (see warmup_tail;
+ * info.k16_from reports the first term stored in 16 bits, K + 1 if none); with
+ * GP_F32 the service stores FP32 only.  The request's y_out must stay valid
+ * until gp_poll reports completion.
  * gp_poll returns GP_OK (and fills info) once the ticket is done, GP_EAGAIN
  * before that, GP_ENOTFOUND for an unknown or already-collected ticket.
  */

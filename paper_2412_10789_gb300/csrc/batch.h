@@ -51,15 +51,18 @@ class ColumnEngine {
   };
 
   // t_long: rows with more entries become chunk tiles (at most kBTileCap;
-  // 0: from cfg.t_heavy, else kBTileCap).
-  ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long = 0);
+  // 0: from cfg.t_heavy, else kBTileCap).  pure16: a 16-bit engine (storage
+  // GP_BF16 or GP_F16) without the FP32 pair, whose columns come only from an
+  // FP32 engine through adopt() once their warm-up is over (the service's
+  // second block); every pass of it gathers, reads and writes 16 bits.
+  ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long = 0, bool pure16 = false);
   int t_long() const { return t_long_; }
   ~ColumnEngine();
   ColumnEngine(const ColumnEngine&) = delete;
   ColumnEngine& operator=(const ColumnEngine&) = delete;
 
   // Device bytes one column occupies (Q pair, 16-bit pair, y).
-  static size_t bytes_per_column(const Graph& g, gp_dtype storage);
+  static size_t bytes_per_column(const Graph& g, gp_dtype storage, bool pure16 = false);
 
   int width() const { return B_; }
   int active() const { return active_; }
@@ -76,6 +79,20 @@ class ColumnEngine {
   std::vector<Finished> collect(bool force_all);
   // Forget the pass count and the 16-bit schedule (no column may be busy).
   void restart();
+  // Busy columns whose stored terms are all past their warm-up: the newest
+  // Q_j has j >= warm + 3, so rounding Q_j and Q_{j-1} to 16 bits keeps every
+  // 16-bit term at index >= warm + 2, where the schedule of gp_batch stores
+  // its first one.  Columns of a pure16 engine are never eligible.
+  std::vector<int> warm_columns() const;
+  // Move columns `cols` of the FP32 engine `src` into free slots of this
+  // pure16 engine (as many as fit; returns how many moved): Q_k and Q_{k-1}
+  // rounded to 16 bits into the buffers this engine's next pass gathers and
+  // reads, y, the column's coefficients, state and last norm, and its request.
+  int adopt(ColumnEngine& src, const std::vector<int>& cols);
+  bool pure16() const { return pure16_; }
+  // An FP32 engine whose columns will move to a 16-bit engine of `storage`:
+  // their warm-up steps follow that storage's threshold (column_warm_tail).
+  void hand_over_to(gp_dtype storage) { warm_storage_ = storage; }
   // Move the busy columns into the first half of the pass width once at most
   // half of it is busy.  Returns whether the width was halved.
   bool compact();
@@ -104,6 +121,9 @@ class ColumnEngine {
     uint64_t tag = 0;
     std::chrono::steady_clock::time_point t_admit;
     std::vector<double> tails;  // FP64 tail(k) for the report
+    uint64_t pass_admit = 0;    // passes_total_ at admission: Q_j, j = 1 + passes since
+    int warm = 0;               // the column's warm-up step (warm_step)
+    int k16_from = -1;          // first term stored in 16 bits once migrated (else -1)
   };
 
   Graph& g_;
@@ -111,6 +131,8 @@ class ColumnEngine {
   int t_long_ = 0;  // rows with more entries are chunk tiles
   int bw_ = 0;  // columns of each pass (a prefix of B_)
   gp_dtype storage_;
+  gp_dtype warm_storage_;  // storage whose warm-up threshold the columns' warm step follows
+  bool pure16_ = false;
   cudaStream_t st_;
   int kcap_ = 0;
   float* f_[2] = {nullptr, nullptr};  // FP32 Q pair
@@ -151,6 +173,13 @@ class ColumnEngine {
   std::vector<cudaEvent_t> events_;
   std::vector<double> prof_marks_;  // algorithmic bytes of each timed pass
 };
+
+// The W(k) threshold below which a column of tolerance tol may store its Q in
+// 16 bits: cfg.warmup_tail for BF16, four times it for FP16 (an 11-bit
+// significand against BF16's 8, with Q * 2^12 clear of the subnormals), each
+// scaled down in proportion to tol below 1e-4 (the 16-bit rounding error that
+// reaches y is proportional to the threshold).
+double column_warm_tail(double warmup_tail, gp_dtype storage, double tol);
 
 struct BatchCache {
   std::unique_ptr<ColumnEngine> eng;

@@ -1,4 +1,4 @@
-// Continuous-batching service (gp_submit / gp_poll / gp_serve_stats).
+// Continuous-batching service (gp_submit / gp_poll / gp_wait / gp_serve_stats).
 //
 // One service thread per graph owns the column engines (batch.h) of its block
 // on its own stream.  The block's width (columns = query slots) is what the
@@ -17,6 +17,15 @@
 // most half of that prefix is busy, so a lightly loaded service runs narrow
 // passes.  Requests therefore join and leave the running block while the
 // others keep going; their work shares every pass.
+//
+// 16-bit storage (cfg.storage GP_BF16 or GP_F16).  Columns join at different
+// passes, so one block cannot switch its storage for all of them at once.
+// The service keeps two blocks of the same width: requests start in an FP32
+// block, and once a column's stored terms are past its own warm-up (the
+// weighted tail W(k) of its coefficients below its threshold, which scales
+// with its tolerance) it moves to a 16-bit block (its Q_k and Q_{k-1} rounded
+// to 16 bits, y kept in FP32), where it runs to its stop.  A column whose
+// 16-bit block is full stays in FP32 until a slot frees up.
 #include <algorithm>
 #include <condition_variable>
 #include <cstring>
@@ -53,7 +62,8 @@ struct Serve {
   Graph* g = nullptr;
   int device = 0;
   cudaStream_t stream = nullptr;
-  std::vector<std::unique_ptr<ColumnEngine>> engs;  // the block's column halves
+  std::vector<std::unique_ptr<ColumnEngine>> engs;  // the FP32 block's column halves (admission)
+  std::vector<std::unique_ptr<ColumnEngine>> engs16;  // the 16-bit block's halves (16-bit storage only)
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Ticket> pending;
@@ -69,6 +79,7 @@ struct Serve {
   int active() const {
     int a = 0;
     for (const auto& e : engs) a += e->active();
+    for (const auto& e : engs16) a += e->active();
     return a;
   }
   int free_slots() const {
@@ -129,22 +140,37 @@ struct Serve {
         // isolated sources are answered at admission
         std::lock_guard<std::mutex> lk(mu);
         for (size_t j = 0; j < slots.size(); ++j)
-          if (slots[j] < 0) finish(t[j], 0, 1.0, 0.0);
+          if (slots[j] < 0) finish(t[j], 0, 1, 1.0, 0.0);
       }
       if (active() > 0) {
         active_sum += active();
         ++passes;
         for (auto& e : engs)
           if (e->active() > 0) e->pass();
+        for (auto& e : engs16)
+          if (e->active() > 0) e->pass();
         if (++since_collect >= kCollectEvery) {
           since_collect = 0;
+          for (auto* list : {&engs, &engs16}) {
+            for (auto& e : *list) {
+              if (e->active() == 0) continue;
+              auto fin = e->collect(false);
+              while (e->active() > 0 && e->compact()) {
+              }
+              std::lock_guard<std::mutex> lk(mu);
+              for (const auto& f : fin) finish(f.tag, f.K, f.k16_from, f.C, f.tail_bound);
+            }
+          }
+          // columns past their warm-up move from the FP32 block to the 16-bit one
           for (auto& e : engs) {
-            if (e->active() == 0) continue;
-            auto fin = e->collect(false);
+            std::vector<int> warm = e->warm_columns();
+            for (auto& h : engs16) {
+              if (warm.empty()) break;
+              const int moved = h->adopt(*e, warm);
+              warm.erase(warm.begin(), warm.begin() + moved);
+            }
             while (e->active() > 0 && e->compact()) {
             }
-            std::lock_guard<std::mutex> lk(mu);
-            for (const auto& f : fin) finish(f.tag, f.K, f.C, f.tail_bound);
           }
         }
       }
@@ -152,13 +178,13 @@ struct Serve {
   }
 
   // mu held
-  void finish(uint64_t id, int K, double C, double bound) {
+  void finish(uint64_t id, int K, int k16_from, double C, double bound) {
     auto it = inflight.find(id);
     Done d;
     d.status = GP_OK;
     std::memset(&d.info, 0, sizeof(d.info));
     d.info.K = K;
-    d.info.k16_from = K + 1;
+    d.info.k16_from = k16_from;
     d.info.max_r_l1 = C;
     d.info.tail_bound = bound;
     if (it != inflight.end()) {
@@ -181,7 +207,10 @@ Serve* get_serve(Graph& g) {
   size_t free_b = 0, total_b = 0;
   GP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = g.cfg.mem_budget ? g.cfg.mem_budget : (size_t)(0.8 * (double)free_b);
-  const size_t per_col = ColumnEngine::bytes_per_column(g, GP_F32);
+  const gp_dtype storage = g.cfg.storage;
+  const bool two_blocks = storage == GP_BF16 || storage == GP_F16;
+  const size_t per_col = ColumnEngine::bytes_per_column(g, GP_F32) +
+                         (two_blocks ? ColumnEngine::bytes_per_column(g, storage, true) : 0);
   // 256 slots already keep the GPU busy on large graphs; more slots add
   // concurrency, not throughput, and lengthen every pass (latency under load)
   const int cap = std::min(g.cfg.block_width > 0 ? g.cfg.block_width : kServeDefaultWidth, kServeMaxWidth);
@@ -189,9 +218,16 @@ Serve* get_serve(Graph& g) {
   while (width * 2 <= cap && (size_t)(width * 2) * per_col <= budget) width *= 2;
   if ((size_t)width * per_col > budget) throw Error{GP_ENOMEM, "memory budget is below eight query columns"};
   // Columns join at different passes, so they cannot share one 16-bit
-  // switch-over: the service stores its blocks in FP32.
-  for (int c0 = 0; c0 < width; c0 += kEngineMaxWidth)
-    s->engs.emplace_back(new ColumnEngine(g, std::min(width - c0, kEngineMaxWidth), GP_F32, s->stream));
+  // switch-over: admission is into FP32 blocks, and with 16-bit storage the
+  // columns move to 16-bit blocks after their own warm-up.
+  for (int c0 = 0; c0 < width; c0 += kEngineMaxWidth) {
+    const int w = std::min(width - c0, kEngineMaxWidth);
+    s->engs.emplace_back(new ColumnEngine(g, w, GP_F32, s->stream));
+    if (two_blocks) {
+      s->engs.back()->hand_over_to(storage);
+      s->engs16.emplace_back(new ColumnEngine(g, w, storage, s->stream, 0, true));
+    }
+  }
   s->th = std::thread([p = s.get()] { p->run(); });
   g.serve = s.release();
   return static_cast<Serve*>(g.serve);
@@ -311,6 +347,7 @@ void serve_shutdown(Graph& g) {
   }
   if (s->th.joinable()) s->th.join();
   s->engs.clear();
+  s->engs16.clear();
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
   g.serve = nullptr;

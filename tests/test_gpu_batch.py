@@ -82,7 +82,8 @@ def test_batch_fixed_K_parity_fp32(gp, B):
 
 
 @pytest.mark.parametrize("gname", ["rmat14", "chunglu20k"])
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-6), ("f32", 1e-4), ("bf16", 1e-4), ("f16", 1e-4)])
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-6), ("f32", 1e-4), ("bf16", 1e-4), ("f16", 1e-4),
+                                         ("bf16", 1e-5), ("bf16", 1e-6), ("f16", 1e-6)])
 def test_batch_stop_rule_accuracy(gp, gname, storage, tol):
     g = graph(gname)
     st = {"f32": gp.GP_F32, "bf16": gp.GP_BF16, "f16": gp.GP_F16}[storage]
@@ -215,10 +216,19 @@ def _serve_all(gp, dg, reqs, timeout=120.0):
     return infos
 
 
-def test_serving_matches_oracle_and_alone(gp):
+STORAGES = {"f32": 0, "bf16": 2, "f16": 3}
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_serving_matches_oracle_and_alone(gp, storage):
+    """Continuous batching: 48 mixed requests through a 16-slot service, each
+    within its tolerance of the oracle and the same alone as in the mix.  With
+    16-bit storage the columns start in the FP32 block and move to the 16-bit
+    block after their own warm-up (k16_from <= K reports it)."""
     g = graph("rmat14")
     srcs = gg.sources(g, 48, 19)
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16,
+                            storage=STORAGES[storage])
     try:
         ys = _outputs(g, len(srcs))
         reqs = []
@@ -230,6 +240,11 @@ def test_serving_matches_oracle_and_alone(gp):
         stats = gp.gp_serve_stats(dg)
         assert stats["completed"] == len(srcs)
         assert stats["mean_active"] > 1.0  # the queries shared passes
+        moved = sum(1 for i, inf in enumerate(infos) if inf["k16_from"] <= inf["K"])
+        if storage == "f32":
+            assert moved == 0
+        else:  # every 1e-4 request outlives its warm-up on this graph
+            assert moved >= len(srcs) // 3, [(inf["K"], inf["k16_from"]) for inf in infos]
         for i, s in enumerate(srcs):
             fn, p = MIX[i % len(MIX)]
             tol = [1e-4, 1e-5, 1e-6][i % 3]
@@ -251,12 +266,15 @@ def test_serving_matches_oracle_and_alone(gp):
         dg.close()
 
 
-def test_serving_512_slots(gp):
-    """A 512-slot block (two 256-column engines): 320 queries at once fill both
-    halves, and every result meets its tolerance."""
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_serving_512_slots(gp, storage):
+    """A 512-slot block (two 256-column engines; with BF16 storage two more
+    16-bit ones): 320 queries at once fill both halves, and every result meets
+    its tolerance."""
     g = graph("rmat14")
     srcs = gg.sources(g, 320, 23)
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=512)
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=512,
+                            storage=STORAGES[storage])
     try:
         ys = _outputs(g, len(srcs))
         reqs = []
