@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--forms", default="single,batched,serving",
                    help="comma list of the forms to time (without 'single' only the named forms run, for "
                         "profiling; the line's value is then null)")
+    p.add_argument("--serve-legs", default="serving,serving_bf16,serving_bf16_tol1e-4",
+                   help="served forms of the rmat22 workload to time")
     p.add_argument("--serve-requests", type=int, default=1024,
                    help="rmat22 serving leg: requests per arrival pattern")
     p.add_argument("--cpu-sample", type=int, default=4,
@@ -204,16 +206,26 @@ def serve_levels(gp, dg, specs, pool, loads, seed, keep=()):
     rng = np.random.default_rng(seed)
     n = len(specs)
     serve_run(gp, dg, specs[: min(n, 64)], np.zeros(min(n, 64)), pool)  # warm-up
-    wall, lat, kept = serve_run(gp, dg, specs, np.zeros(n), pool, keep)
+
+    def passes_of(run):
+        """run() plus the service's passes and mean active columns over it."""
+        s0 = gp.gp_serve_stats(dg)
+        out = run()
+        s1 = gp.gp_serve_stats(dg)
+        steps = s1["steps"] - s0["steps"]
+        act = s1["mean_active"] * s1["steps"] - s0["mean_active"] * s0["steps"]
+        return out, {"passes": steps, "mean_active_columns": act / max(steps, 1)}
+
+    (wall, lat, kept), st = passes_of(lambda: serve_run(gp, dg, specs, np.zeros(n), pool, keep))
     sat = n / wall
     res = {"saturated": {"value": sat, "unit": UNIT, "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99)), "requests": n}}
+                         "p99_ms": float(np.percentile(lat, 99)), "requests": n, **st}}
     for load in loads:
         gaps = rng.exponential(1.0 / (load * sat), n)
-        wall, lat, _ = serve_run(gp, dg, specs, np.cumsum(gaps), pool)
+        (wall, lat, _), st = passes_of(lambda: serve_run(gp, dg, specs, np.cumsum(gaps), pool))
         res[f"load_{load:g}"] = {"offered": load * sat, "value": n / wall, "unit": UNIT,
                                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                                 "requests": n}
+                                 "requests": n, **st}
     stats = gp.gp_serve_stats(dg)
     res["mean_active_columns"] = stats["mean_active"]
     return res, kept
@@ -606,14 +618,18 @@ def run_ours(args, rank, world):
         captured.update(outs)
     serving = {}
     if not args.no_batched and "serving" in forms:
+        legs = set(args.serve_legs.split(","))
         for name, storage, tols in (("serving", "fp32", (1e-4, 1e-5, 1e-6)),
                                     ("serving_bf16", "bf16", (1e-4, 1e-5, 1e-6)),
+                                    ("serving_fp32_tol1e-4", "fp32", (1e-4,)),
                                     ("serving_bf16_tol1e-4", "bf16", (1e-4,))):
+            if name not in legs:
+                continue
             serving[name], outs = bench_serving(gp, g, queries, dev, world, nreq=args.serve_requests, sample=sample,
                                                 storage=storage, tols=tols, name=name)
             captured.update(outs)
         single4 = (batched or {}).get("bf16_tol1e-4", {}).get("single_source_same_tol")
-        if single4:
+        if single4 and "serving_bf16_tol1e-4" in serving:
             serving["serving_bf16_tol1e-4"]["single_source_same_tol"] = single4
             serving["serving_bf16_tol1e-4"]["vs_single_source_same_tol"] = \
                 serving["serving_bf16_tol1e-4"]["saturated"]["value"] / single4

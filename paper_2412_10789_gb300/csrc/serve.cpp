@@ -149,27 +149,33 @@ struct Serve {
           if (e->active() > 0) e->pass();
         for (auto& e : engs16)
           if (e->active() > 0) e->pass();
+        // columns past their warm-up move from the FP32 block to the 16-bit one
+        // (decided from the host's pass counts, so no wait on the device)
+        for (auto& e : engs) {
+          std::vector<int> warm = e->warm_columns();
+          for (auto& h : engs16) {
+            if (warm.empty()) break;
+            const int moved = h->adopt(*e, warm);
+            warm.erase(warm.begin(), warm.begin() + moved);
+          }
+        }
         if (++since_collect >= kCollectEvery) {
           since_collect = 0;
+          bool queued = false;
+          {
+            std::lock_guard<std::mutex> lk(mu);
+            queued = !pending.empty();
+          }
           for (auto* list : {&engs, &engs16}) {
             for (auto& e : *list) {
               if (e->active() == 0) continue;
               auto fin = e->collect(false);
-              while (e->active() > 0 && e->compact()) {
+              // narrow the passes of a lightly loaded block; with requests
+              // waiting, the freed columns refill at once instead
+              while (!queued && e->active() > 0 && e->compact()) {
               }
               std::lock_guard<std::mutex> lk(mu);
               for (const auto& f : fin) finish(f.tag, f.K, f.k16_from, f.C, f.tail_bound);
-            }
-          }
-          // columns past their warm-up move from the FP32 block to the 16-bit one
-          for (auto& e : engs) {
-            std::vector<int> warm = e->warm_columns();
-            for (auto& h : engs16) {
-              if (warm.empty()) break;
-              const int moved = h->adopt(*e, warm);
-              warm.erase(warm.begin(), warm.begin() + moved);
-            }
-            while (e->active() > 0 && e->compact()) {
             }
           }
         }
