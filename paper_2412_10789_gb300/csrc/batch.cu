@@ -300,6 +300,8 @@ struct SpmmArgs {
   int check;            // col_idx lists rows beyond the active ones (host: picks the kernel)
   int* tile_ctr;        // tiles claimed past the first three per warp (zeroed by the control kernel)
   int mode;             // kModeForward, kModeClenshaw or kModeClenshawFinal
+  const int* Bdev = nullptr;        // non-null: the pass width is read here (set on the device), B is its cap
+  const int* active_dev = nullptr;  // non-null: the pass returns at once while this count of busy columns is 0
 };
 
 // Combine the entry groups' partial sums (lanes cg, cg + CG, cg + 2 CG, ...).
@@ -344,6 +346,7 @@ struct Lane {
   uint32_t rowG, rowP, rowN, rowY;  // row bytes of Q_k, Q_{k-1}, Q_{k+1}, y
   int na;
   int mode;                     // kMode*: which row update the pass applies
+  int B;                        // columns of this pass
   int cg, g, CG, EG, lane;
 };
 
@@ -608,7 +611,7 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
 #pragma unroll
   for (int i = 0; i < LC; ++i) tot[i] = 0.f;
   for (int i = L.g; i < np; i += L.EG) {
-    const float4* src = reinterpret_cast<const float4*>(a.part + (int64_t)(slot0 + i) * a.B + L.cg * LC);
+    const float4* src = reinterpret_cast<const float4*>(a.part + (int64_t)(slot0 + i) * L.B + L.cg * LC);
 #pragma unroll
     for (int q = 0; q < LC / 4; ++q) {
       const float4 x = __ldcg(src + q);
@@ -672,7 +675,7 @@ __device__ __forceinline__ void publish_chunk(const Lane& L, const BTile& t, flo
   const int64_t row = t.row0;
   const int slot0 = a.poff[row], np = a.poff[row + 1] - slot0;
   if (L.g == 0) {
-    float4* dst = reinterpret_cast<float4*>(a.part + (int64_t)(slot0 + t.a) * a.B + L.cg * LC);
+    float4* dst = reinterpret_cast<float4*>(a.part + (int64_t)(slot0 + t.a) * L.B + L.cg * LC);
 #pragma unroll
     for (int i = 0; i < LC / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
   }
@@ -821,20 +824,23 @@ template <typename TG, typename TP, typename TO, int LC, bool CHECK>
 __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __grid_constant__ SpmmArgs a) {
   using C = Geo<TG, TP, TO, LC>;
   extern __shared__ __align__(16) unsigned char s_raw[];
+  if (a.active_dev && *a.active_dev == 0) return;  // no busy column (set on the device)
+  const int B = a.Bdev ? *a.Bdev : a.B;
   ColState* s_col = reinterpret_cast<ColState*>(s_raw);
-  float* s_norm = reinterpret_cast<float*>(s_raw + sizeof(ColState) * a.B);
+  float* s_norm = reinterpret_cast<float*>(s_raw + sizeof(ColState) * B);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* ring = s_raw + kHeaderBytes + (size_t)warp * 32 * kRingLaneBytes;
   int* s_ci = reinterpret_cast<int*>(s_raw + kHeaderBytes + (size_t)kBatchWarps * 32 * kRingLaneBytes) +
               warp * 2 * kBTileSpan;
-  for (int j = threadIdx.x; j < a.B; j += blockDim.x) {
+  for (int j = threadIdx.x; j < B; j += blockDim.x) {
     s_col[j] = a.col[j];
     s_norm[j] = 0.f;
   }
   __syncthreads();
   Lane L;
   L.a = &a;
-  L.CG = a.B / LC;
+  L.B = B;
+  L.CG = B / LC;
   L.EG = 32 / L.CG;
   L.cg = lane % L.CG;
   L.g = lane / L.CG;
@@ -905,7 +911,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   for (int i = 0; i < LC; ++i)
     if (nrm[i] != 0.f) atomicAdd(&s_norm[L.cg * LC + i], nrm[i]);
   __syncthreads();
-  for (int j = threadIdx.x; j < a.B; j += blockDim.x)
+  for (int j = threadIdx.x; j < B; j += blockDim.x)
     if (s_norm[j] != 0.f) atomicAdd(&a.norm[j], s_norm[j]);
 }
 
@@ -1227,7 +1233,11 @@ void launch_stage(const SpmmArgs& a, int stage, cudaStream_t st) {
 
 // ------------------------------------------------------------------ engine
 
-namespace {
+double column_warm_tail(double warmup_tail, gp_dtype storage, double tol) {
+  const double base = storage == GP_F16 ? 4.0 * warmup_tail : warmup_tail;
+  return base * std::min(1.0, tol / 1e-4);
+}
+
 // The first step whose Q may be stored in 16 bits: the smallest k with
 // W(k) = sum_{m>=0} (m + 1) |c_{k+1+m}| < warmup_tail.  A rounding error that
 // the recurrence does not compensate propagates with the second-kind
@@ -1236,14 +1246,6 @@ namespace {
 // error made at step k reaches y weighted by W(k) rather than by the tail
 // sum_{l>k} |c_l| (which let slowly decaying expansions, SSPPR alpha = 0.1,
 // pass l1 = 1e-4 in 16-bit blocks).  kcap when no step qualifies.
-}  // namespace
-
-double column_warm_tail(double warmup_tail, gp_dtype storage, double tol) {
-  const double base = storage == GP_F16 ? 4.0 * warmup_tail : warmup_tail;
-  return base * std::min(1.0, tol / 1e-4);
-}
-
-namespace {
 int warm_step(const std::vector<double>& c, int kcap, double warmup_tail) {
   const int last = (int)c.size() - 1;
   for (int k = 0; k <= kcap && k < kMaxColK; ++k) {
@@ -1253,7 +1255,6 @@ int warm_step(const std::vector<double>& c, int kcap, double warmup_tail) {
   }
   return std::min(kcap, kMaxColK - 1);
 }
-}  // namespace
 
 ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long, bool pure16)
     : g_(g), B_(B), bw_(B), storage_(storage), warm_storage_(storage), pure16_(pure16), st_(st) {
@@ -2316,6 +2317,58 @@ std::vector<ColumnEngine::Finished> ColumnEngine::propagate(const float* X, floa
   }
   prop_.on = false;
   return fin;
+}
+
+ColumnEngine::View ColumnEngine::view() const {
+  View v;
+  v.f[0] = f_[0];
+  v.f[1] = f_[1];
+  v.h[0] = h_[0];
+  v.h[1] = h_[1];
+  v.y = y_;
+  v.col = col_;
+  v.par = par_;
+  v.stat = stat_;
+  v.norm = norm_;
+  v.B = B_;
+  v.pass = pass_;
+  v.storage = storage_;
+  v.pure16 = pure16_;
+  return v;
+}
+
+void ColumnEngine::pass_device(const int* width_dev, const int* active_dev) {
+  if (storage_ != GP_F32 && !pure16_) throw Error{GP_EINVAL, "device-width passes run FP32 or pure 16-bit engines"};
+  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_);
+  GP_LAUNCHED();
+  SpmmArgs a;
+  a.tiles = tiles_;
+  a.ntiles = ntiles_;
+  a.ci = g_.ci;
+  const int cur = pass_ & 1, nxt = (pass_ + 1) & 1;
+  a.qcur = pure16_ ? h_[cur] : (const void*)f_[cur];
+  a.qprev = pure16_ ? h_[nxt] : (const void*)f_[nxt];
+  a.qnext = pure16_ ? h_[nxt] : (void*)f_[nxt];
+  a.y = y_;
+  a.col = col_;
+  a.norm = norm_;
+  a.poff = poff_;
+  a.ldeg = ldeg_;
+  a.part = part_;
+  a.cnt = cnt_;
+  a.zero = zero_;
+  a.na = g_.n_active;
+  a.B = B_;  // the cap: it picks the columns per lane, so the device width is at least min_width()
+  a.ldb = B_;
+  a.check = g_.ci_beyond_active ? 1 : 0;
+  a.tile_ctr = tile_ctr_;
+  a.mode = kModeForward;
+  a.Bdev = width_dev;
+  a.active_dev = active_dev;
+  if (storage_ == GP_F16) launch_stage<__half>(a, pure16_ ? 3 : 0, st_);
+  else launch_stage<__nv_bfloat16>(a, pure16_ ? 3 : 0, st_);
+  ++pass_;
+  ++passes_total_;
 }
 
 std::vector<int> ColumnEngine::warm_columns() const {

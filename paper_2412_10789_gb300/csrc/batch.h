@@ -90,6 +90,27 @@ class ColumnEngine {
   // reads, y, the column's coefficients, state and last norm, and its request.
   int adopt(ColumnEngine& src, const std::vector<int>& cols);
   bool pure16() const { return pure16_; }
+  // Device arrays of the engine, for the device-resident service (ring.cu).
+  struct View {
+    float* f[2];      // FP32 pair (null in a pure16 engine)
+    void* h[2];       // 16-bit pair (null in an FP32 engine)
+    float* y;
+    ColState* col;
+    ColParam* par;
+    ColStat* stat;
+    float* norm;
+    int B;
+    int pass;         // index of the next pass: it gathers buffer pass & 1
+    gp_dtype storage;
+    bool pure16;
+  };
+  View view() const;
+  // One pass whose width and busy-column count are read from device memory
+  // (set by the service's kernels): the control kernel, then the fused SpMM
+  // step, which returns at once while no column is busy.
+  void pass_device(const int* width_dev, const int* active_dev);
+  // Smallest pass width the engine's kernels accept (a 16-bit lane owns 16 columns).
+  int min_width() const { return pure16_ && B_ >= 16 ? 16 : 8; }
   // An FP32 engine whose columns will move to a 16-bit engine of `storage`:
   // their warm-up steps follow that storage's threshold (column_warm_tail).
   void hand_over_to(gp_dtype storage) { warm_storage_ = storage; }
@@ -180,6 +201,9 @@ class ColumnEngine {
 // scaled down in proportion to tol below 1e-4 (the 16-bit rounding error that
 // reaches y is proportional to the threshold).
 double column_warm_tail(double warmup_tail, gp_dtype storage, double tol);
+// The first step k whose W(k) = sum_{m>=0} (m + 1) |c_{k+1+m}| is below the
+// threshold (kcap when none): Q_j with j >= k + 2 may be stored in 16 bits.
+int warm_step(const std::vector<double>& c, int kcap, double warmup_tail);
 
 struct BatchCache {
   std::unique_ptr<ColumnEngine> eng;

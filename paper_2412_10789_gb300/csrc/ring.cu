@@ -1,0 +1,534 @@
+// Device-resident request loop of the continuous-batching service.
+//
+// The service's requests and results travel through two rings in pinned,
+// mapped host memory that the GPU reads and writes directly:
+//   request ring  (host -> device): one RingReq per request, published by
+//                 the service thread with a release store of ctl.tail;
+//   done ring     (device -> host): one RingDone per finished query, made
+//                 visible by a release store of ctl.done after the output
+//                 kernel has written the query's y.
+// Every iteration is the same fixed sequence of kernels, launched without any
+// wait for the device in between:
+//   admit    (one block)  takes requests off the request ring into the free
+//                          columns of the FP32 block: coefficients, state,
+//                          source and output pointer of each new column;
+//   reset + init          zero the new columns, r_0 = e_s, r_1 = P e_s;
+//   width    (one block)  per block, the pass width from its busiest slot;
+//   control + SpMM        the fused pass of each block (Algorithm 3's step
+//                          with the per-column stop rule of Theorem 1);
+//   retire   (one block)  per block, the columns whose stop rule fired;
+//   output                their y into the caller's (or a staging) buffer;
+//   complete (one block)  their RingDone records, then frees their columns;
+//   migrate               (16-bit storage) columns past their own warm-up
+//                          move from the FP32 block to the 16-bit block.
+// So admission into free slots, packing as columns of one SpMM, per-column
+// retirement and the refill of freed slots are all decided on the device.
+// The host thread only publishes requests, launches iterations (at most two
+// queued ahead of the GPU) and turns done records into completed tickets.
+#include <cuda/atomic>
+
+#include <algorithm>
+#include <cstring>
+
+#include "ring.h"
+
+namespace gp {
+
+namespace {
+
+__device__ __forceinline__ uint64_t load_acquire_sys(const uint64_t* p) {
+  return cuda::atomic_ref<uint64_t, cuda::thread_scope_system>(*const_cast<uint64_t*>(p))
+      .load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void store_release_sys(uint64_t* p, uint64_t v) {
+  cuda::atomic_ref<uint64_t, cuda::thread_scope_system>(*p).store(v, cuda::memory_order_release);
+}
+
+constexpr int kRingThreads = 256;  // one thread per column slot (blocks of at most 256 columns)
+
+// Exclusive prefix sum of flag over the block; returns the rank, total in *tot.
+__device__ __forceinline__ int block_rank(int flag, int* s_scan, int* tot) {
+  const int t = threadIdx.x;
+  s_scan[t] = flag;
+  __syncthreads();
+  for (int off = 1; off < kRingThreads; off <<= 1) {
+    const int v = t >= off ? s_scan[t - off] : 0;
+    __syncthreads();
+    s_scan[t] += v;
+    __syncthreads();
+  }
+  const int incl = s_scan[t];
+  *tot = s_scan[kRingThreads - 1];
+  __syncthreads();
+  return incl - flag;
+}
+
+// Requests off the ring into free columns of the FP32 block (lowest free
+// slots first).  New columns: r_0 = e_s, r_1 = P e_s (set by the init
+// kernel), k = 1, ||r_0||_1 = ||r_1||_1 = 1.
+__global__ void __launch_bounds__(kRingThreads) ring_admit_kernel(RingCtl* ctl, const RingReq* ring, int cap,
+                                                                  RingDev* dev, SlotDev* slots, ColState* col,
+                                                                  ColParam* par, ColStat* stat, float* norm, int B,
+                                                                  int* new_list) {
+  __shared__ int s_scan[kRingThreads];
+  __shared__ int s_take;
+  __shared__ uint64_t s_head;
+  const int j = threadIdx.x;
+  const int free_slot = j < B && !slots[j].busy;
+  int nfree = 0;
+  const int rank = block_rank(free_slot, s_scan, &nfree);
+  if (j == 0) {
+    const uint64_t tail = load_acquire_sys(&ctl->tail);
+    const uint64_t head = dev->head;
+    s_head = head;
+    s_take = (int)std::min<uint64_t>(tail - head, (uint64_t)nfree);
+  }
+  __syncthreads();
+  const int take = s_take;
+  if (free_slot && rank < take) {
+    (void)load_acquire_sys(&ctl->tail);  // this thread's reads of the entry follow the host's publication
+    const RingReq& r = ring[(s_head + rank) % cap];
+    SlotDev sd;
+    sd.ticket = r.ticket;
+    sd.out = r.out;
+    sd.src = r.src;
+    sd.busy = 1;
+    sd.out_f64 = r.out_f64;
+    sd.warm = r.param.warm;
+    sd.k16 = -1;
+    slots[j] = sd;
+    col[j] = ColState{1, 0.f};
+    stat[j] = ColStat{1, 0, 0, 1.0f};
+    norm[j] = 0.f;
+    new_list[rank] = j;
+  }
+  __syncthreads();
+  // the coefficient tables, one column at a time by the whole block
+  constexpr int kWords = (int)(sizeof(ColParam) / sizeof(float));
+  for (int t = 0; t < take; ++t) {
+    const float* from = reinterpret_cast<const float*>(&ring[(s_head + t) % cap].param);
+    float* to = reinterpret_cast<float*>(par + new_list[t]);
+    for (int i = j; i < kWords; i += kRingThreads) to[i] = from[i];
+  }
+  if (j == 0) {
+    dev->new_count = take;
+    dev->head = s_head + take;
+    dev->active32 += take;
+    store_release_sys(&ctl->head, s_head + take);
+  }
+}
+
+// Zero the new columns of Q_a, Q_b and y over all rows (a warp per row).
+__global__ void ring_reset_kernel(int64_t na, int B, const int* new_list, const RingDev* dev, float* fa, float* fb,
+                                  float* y) {
+  const int nc = dev->new_count;
+  if (nc == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
+    for (int t = lane; t < nc; t += 32) {
+      const int64_t i = r * B + new_list[t];
+      fa[i] = 0.f;
+      fb[i] = 0.f;
+      y[i] = 0.f;
+    }
+  }
+}
+
+// r_0 = e_s (Q_0 = e_s / d_s), r_1 = P e_s (Q_1(v) = 1 / (d_s d_v) for v in
+// N(s) with d_v > 0), y = c_0 r_0 + c_1 r_1, for the new column of this block.
+template <typename RP>
+__global__ void ring_init_kernel(const void* rpv, const int32_t* ci, int64_t na, int B, const int* new_list,
+                                 const RingDev* dev, const SlotDev* slots, const ColParam* par, float* q0, float* q1,
+                                 float* y) {
+  if ((int)blockIdx.x >= dev->new_count) return;
+  const RP* rp = (const RP*)rpv;
+  const int j = new_list[blockIdx.x];
+  const int64_t s = slots[j].src;
+  const int64_t beg = rp[s], end = rp[s + 1];
+  const float ds = (float)(end - beg);
+  const float c0 = par[j].c[0], c1 = par[j].c[1];
+  if (threadIdx.x == 0) {
+    q0[s * B + j] = 1.0f / ds;
+    y[s * B + j] = c0;
+  }
+  for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    const int32_t v = ci[e];
+    if (v >= na) continue;  // only an unvalidated asymmetric CSR lists an isolated row
+    const float dv = (float)(rp[v + 1] - rp[v]);
+    q1[(int64_t)v * B + j] = (float)(1.0 / ((double)ds * (double)dv));
+    y[(int64_t)v * B + j] = c1 / ds;
+  }
+}
+
+// The pass width of a block: the smallest power of two (at least min_w, at
+// most B) that holds its highest busy slot.
+__global__ void __launch_bounds__(kRingThreads) ring_width_kernel(const SlotDev* slots, int B, int min_w,
+                                                                  int* width) {
+  __shared__ int s_max;
+  if (threadIdx.x == 0) s_max = -1;
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < B && slots[j].busy) atomicMax(&s_max, j);
+  __syncthreads();
+  if (j == 0) {
+    int w = min_w;
+    while (w < s_max + 1) w <<= 1;
+    *width = std::min(w, B);
+  }
+}
+
+// Columns of a block whose stop rule fired, as many as the done ring has room
+// for (the rest stay until the host has read more records).
+__global__ void __launch_bounds__(kRingThreads) ring_retire_kernel(const RingCtl* ctl, const RingDev* dev, int cap,
+                                                                   const SlotDev* slots, const ColStat* stat, int B,
+                                                                   int* ret_list, int* ret_count) {
+  __shared__ int s_scan[kRingThreads];
+  const int j = threadIdx.x;
+  const int fin = j < B && slots[j].busy && stat[j].done;
+  int nfin = 0;
+  const int rank = block_rank(fin, s_scan, &nfin);
+  const uint64_t used = dev->done - load_acquire_sys(&ctl->consumed);
+  const int room = used >= (uint64_t)cap ? 0 : (int)std::min<uint64_t>((uint64_t)cap - used, (uint64_t)nfin);
+  if (fin && rank < room) ret_list[rank] = j;
+  if (j == 0) *ret_count = room;
+}
+
+// y of the retired columns (relabelled rows) into their outputs in the
+// caller's numbering, for the columns whose output type is OUT: a CTA copies
+// 32 rows of y into shared memory, then writes each column's 32 values.
+template <typename OUT>
+__global__ void ring_output_kernel(int64_t n, int64_t na, const int32_t* newid, const float* y, int B,
+                                   const int* ret_list, const int* ret_count, const SlotDev* slots) {
+  const int nc = *ret_count;
+  if (nc == 0) return;
+  extern __shared__ __align__(16) float s_tile[];  // 32 x B
+  __shared__ int64_t s_row[32];
+  __shared__ int s_any;
+  constexpr int kF64 = sizeof(OUT) == 8;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < nc; t += blockDim.x)
+    if (slots[ret_list[t]].out_f64 == kF64) s_any = 1;
+  __syncthreads();
+  if (!s_any) return;  // no retired column wants this output type
+  for (int64_t u0 = (int64_t)blockIdx.x * 32; u0 < n; u0 += (int64_t)gridDim.x * 32) {
+    if (threadIdx.x < 32) {
+      const int64_t u = u0 + threadIdx.x;
+      s_row[threadIdx.x] = u < n ? (int64_t)newid[u] : -1;
+    }
+    __syncthreads();
+    const int nvec = 32 * (B / 4);
+    for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+      const int r = v / (B / 4), c4 = v % (B / 4);
+      const int64_t i = s_row[r];
+      const float4 val = (i >= 0 && i < na) ? *reinterpret_cast<const float4*>(y + i * B + 4 * c4)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(s_tile + r * B + 4 * c4) = val;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t u = u0 + lane;
+    for (int t = warp; t < nc; t += nw) {
+      const int j = ret_list[t];
+      if (slots[j].out_f64 != kF64) continue;
+      if (u < n) static_cast<OUT*>(slots[j].out)[u] = (OUT)s_tile[lane * B + j];
+    }
+    __syncthreads();
+  }
+}
+
+// Done records of the retired columns (after their outputs), then their
+// columns are freed for the next admission.
+__global__ void __launch_bounds__(kRingThreads) ring_complete_kernel(RingCtl* ctl, RingDone* done_ring, int cap,
+                                                                     RingDev* dev, SlotDev* slots, ColState* col,
+                                                                     ColStat* stat, float* norm, const int* ret_list,
+                                                                     const int* ret_count, int block16) {
+  const int nc = *ret_count;
+  if (nc == 0) return;
+  const uint64_t base = dev->done;
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    const int j = ret_list[t];
+    const ColStat st = stat[j];
+    RingDone d;
+    d.ticket = slots[j].ticket;
+    d.K = st.done ? st.K : st.k;
+    d.k16_from = slots[j].k16 >= 0 ? slots[j].k16 : d.K + 1;
+    d.C = st.C;
+    d.pad = 0;
+    done_ring[(base + t) % cap] = d;
+    slots[j].busy = 0;
+    col[j] = ColState{0, 0.f};
+    stat[j] = ColStat{0, 0, 0, 0.f};
+    norm[j] = 0.f;
+  }
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dev->done = base + nc;
+    if (block16)
+      dev->active16 -= nc;
+    else
+      dev->active32 -= nc;
+    store_release_sys(&ctl->done, base + nc);
+  }
+}
+
+// FP32 columns past their own warm-up (newest term Q_k with k >= warm + 3, so
+// every 16-bit term has index >= warm + 2) paired with free 16-bit slots; the
+// slot records move with them.
+__global__ void __launch_bounds__(kRingThreads) ring_migrate_select_kernel(RingDev* dev, SlotDev* s32,
+                                                                           const ColStat* st32, int B32, SlotDev* s16,
+                                                                           int B16, int* from, int* to) {
+  __shared__ int s_scan[kRingThreads];
+  __shared__ int s_from[kRingThreads];
+  __shared__ int s_to[kRingThreads];
+  const int j = threadIdx.x;
+  const int cand = j < B32 && s32[j].busy && !st32[j].done && st32[j].k >= s32[j].warm + 3;
+  int ncand = 0;
+  const int rc = block_rank(cand, s_scan, &ncand);
+  if (cand) s_from[rc] = j;
+  const int fr = j < B16 && !s16[j].busy;
+  int nfree = 0;
+  const int rf = block_rank(fr, s_scan, &nfree);
+  if (fr) s_to[rf] = j;
+  __syncthreads();
+  const int take = std::min(ncand, nfree);
+  if (j < take) {
+    const int a = s_from[j], b = s_to[j];
+    SlotDev sd = s32[a];
+    sd.k16 = st32[a].k - 1;  // Q_k and Q_{k-1} are rounded: the first 16-bit term is Q_{k-1}
+    s16[b] = sd;
+    s32[a].busy = 0;
+    from[j] = a;
+    to[j] = b;
+  }
+  if (j == 0) {
+    dev->mig_count = take;
+    dev->active32 -= take;
+    dev->active16 += take;
+  }
+}
+
+template <typename H>
+__device__ __forceinline__ H ring_to16(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 ring_to16<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half ring_to16<__half>(float x) { return __float2half_rn(x * 4096.0f); }
+
+// Q_k, Q_{k-1} (rounded as the 16-bit passes store them: BF16 round to nearest,
+// FP16 of Q * 2^12) and y of the selected columns, a warp per row.
+template <typename H>
+__global__ void ring_migrate_columns_kernel(int64_t na, int ldb_s, int ldb_d, const int* from, const int* to,
+                                            const RingDev* dev, const float* fk, const float* fk1, const float* ys,
+                                            H* hk, H* hk1, float* yd) {
+  const int nc = dev->mig_count;
+  if (nc == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
+    for (int t = lane; t < nc; t += 32) {
+      const int64_t a = r * ldb_s + from[t], b = r * ldb_d + to[t];
+      hk[b] = ring_to16<H>(fk[a]);
+      hk1[b] = ring_to16<H>(fk1[a]);
+      yd[b] = ys[a];
+    }
+  }
+}
+
+// The moved columns' coefficients, state and last norm (a block per column);
+// the FP32 column is cleared.
+__global__ void ring_migrate_state_kernel(const int* from, const int* to, const RingDev* dev, ColState* cs_s,
+                                          const ColParam* cp_s, ColStat* st_s, float* nm_s, ColState* cs_d,
+                                          ColParam* cp_d, ColStat* st_d, float* nm_d) {
+  if ((int)blockIdx.x >= dev->mig_count) return;
+  const int a = from[blockIdx.x], b = to[blockIdx.x];
+  const float* src = reinterpret_cast<const float*>(cp_s + a);
+  float* dst = reinterpret_cast<float*>(cp_d + b);
+  for (int i = threadIdx.x; i < (int)(sizeof(ColParam) / sizeof(float)); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cs_d[b] = cs_s[a];
+    st_d[b] = st_s[a];
+    nm_d[b] = nm_s[a];
+    cs_s[a] = ColState{0, 0.f};
+    st_s[a] = ColStat{0, 0, 0, 0.f};
+    nm_s[a] = 0.f;
+  }
+}
+
+// Busy columns of both blocks after the iteration, for the host's statistics.
+__global__ void ring_stats_kernel(RingCtl* ctl, const RingDev* dev) {
+  ctl->active = dev->active32 + dev->active16;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+int ring_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+template <typename T>
+void mapped_alloc(T** host, T** dev, size_t count) {
+  GP_CUDA_TRY(cudaHostAlloc((void**)host, sizeof(T) * count, cudaHostAllocMapped | cudaHostAllocPortable));
+  std::memset((void*)*host, 0, sizeof(T) * count);
+  GP_CUDA_TRY(cudaHostGetDevicePointer((void**)dev, (void*)*host, 0));
+}
+
+}  // namespace
+
+RingLoop::RingLoop(Graph& g, int width, gp_dtype storage, cudaStream_t st) : g_(g), B_(width), st_(st) {
+  if (width < 8 || width > kRingThreads) throw Error{GP_EINVAL, "a ring block has 8 to 256 columns"};
+  try {
+    const bool two = storage == GP_BF16 || storage == GP_F16;
+    e32_.reset(new ColumnEngine(g, width, GP_F32, st));
+    if (two) {
+      e32_->hand_over_to(storage);
+      e16_.reset(new ColumnEngine(g, width, storage, st, 0, true));
+    }
+    cap_req_ = 1024;
+    cap_done_ = 4096;
+    mapped_alloc(&ctl_, &ctl_d_, 1);
+    mapped_alloc(&req_, &req_d_, (size_t)cap_req_);
+    mapped_alloc(&done_, &done_d_, (size_t)cap_done_);
+    const size_t bytes = sizeof(RingDev) + 2 * kRingThreads * sizeof(SlotDev) + (5 * kRingThreads + 4) * sizeof(int);
+    dmem_ = g.alloc.get(bytes);
+    GP_CUDA_TRY(cudaMemsetAsync(dmem_, 0, bytes, st_));
+    GP_CUDA_TRY(cudaStreamSynchronize(st_));
+    unsigned char* p = static_cast<unsigned char*>(dmem_);
+    dev_ = reinterpret_cast<RingDev*>(p);
+    p += sizeof(RingDev);
+    slots32_ = reinterpret_cast<SlotDev*>(p);
+    p += kRingThreads * sizeof(SlotDev);
+    slots16_ = reinterpret_cast<SlotDev*>(p);
+    p += kRingThreads * sizeof(SlotDev);
+    int* ip = reinterpret_cast<int*>(p);
+    new_list_ = ip;
+    ret32_ = ip + kRingThreads;
+    ret16_ = ip + 2 * kRingThreads;
+    mig_from_ = ip + 3 * kRingThreads;
+    mig_to_ = ip + 4 * kRingThreads;
+    cnt_ = ip + 5 * kRingThreads;
+  } catch (...) {
+    release();
+    throw;
+  }
+}
+
+RingLoop::~RingLoop() { release(); }
+
+void RingLoop::release() {
+  if (st_) cudaStreamSynchronize(st_);
+  e16_.reset();
+  e32_.reset();
+  if (ctl_) cudaFreeHost(ctl_);
+  if (req_) cudaFreeHost(req_);
+  if (done_) cudaFreeHost(done_);
+  ctl_ = nullptr;
+  req_ = nullptr;
+  done_ = nullptr;
+  if (dmem_) g_.alloc.put(dmem_);
+  dmem_ = nullptr;
+}
+
+int RingLoop::room() const {
+  const uint64_t head = __atomic_load_n(&ctl_->head, __ATOMIC_ACQUIRE);
+  return cap_req_ - (int)(tail_ - head);
+}
+
+void RingLoop::publish(const RingReq& r) {
+  std::memcpy((void*)&req_[tail_ % (uint64_t)cap_req_], &r, sizeof(RingReq));
+  ++tail_;
+  __atomic_store_n(&ctl_->tail, tail_, __ATOMIC_RELEASE);
+}
+
+void RingLoop::take_done(std::vector<RingDone>& out) {
+  const uint64_t done = __atomic_load_n(&ctl_->done, __ATOMIC_ACQUIRE);
+  for (uint64_t c = consumed_; c < done; ++c) out.push_back(done_[c % (uint64_t)cap_done_]);
+  consumed_ = done;
+  __atomic_store_n(&ctl_->consumed, consumed_, __ATOMIC_RELEASE);
+}
+
+int RingLoop::active() const { return __atomic_load_n(&ctl_->active, __ATOMIC_RELAXED); }
+
+void RingLoop::iterate() {
+  const int sms = ring_sms();
+  const int64_t na = g_.n_active;
+  ColumnEngine::View v = e32_->view();
+  // admission into the FP32 block: records, reset and r_0, r_1 of the new columns
+  ring_admit_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, req_d_, cap_req_, dev_, slots32_, v.col, v.par, v.stat,
+                                                 v.norm, B_, new_list_);
+  GP_LAUNCHED();
+  ring_reset_kernel<<<sms * 8, 256, 0, st_>>>(na, B_, new_list_, dev_, v.f[0], v.f[1], v.y);
+  GP_LAUNCHED();
+  float* q1 = v.f[v.pass & 1];
+  float* q0 = v.f[(v.pass + 1) & 1];
+  if (g_.rp64)
+    ring_init_kernel<int64_t><<<B_, 256, 0, st_>>>(g_.rp, g_.ci, na, B_, new_list_, dev_, slots32_, v.par, q0, q1, v.y);
+  else
+    ring_init_kernel<int32_t><<<B_, 256, 0, st_>>>(g_.rp, g_.ci, na, B_, new_list_, dev_, slots32_, v.par, q0, q1, v.y);
+  GP_LAUNCHED();
+  // one fused pass of each block, at the width its busy slots need
+  ring_width_kernel<<<1, kRingThreads, 0, st_>>>(slots32_, B_, e32_->min_width(), cnt_ + 2);
+  GP_LAUNCHED();
+  e32_->pass_device(cnt_ + 2, &dev_->active32);
+  if (e16_) {
+    ring_width_kernel<<<1, kRingThreads, 0, st_>>>(slots16_, B_, e16_->min_width(), cnt_ + 3);
+    GP_LAUNCHED();
+    e16_->pass_device(cnt_ + 3, &dev_->active16);
+  }
+  // retirement: outputs, done records, freed columns
+  const size_t smem = sizeof(float) * 32 * B_;
+  auto retire = [&](ColumnEngine& e, SlotDev* slots, int* ret, int* count, int block16) {
+    const ColumnEngine::View w = e.view();
+    ring_retire_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, dev_, cap_done_, slots, w.stat, B_, ret, count);
+    GP_LAUNCHED();
+    ring_output_kernel<double><<<sms * 4, 256, smem, st_>>>(g_.n, na, g_.newid, w.y, B_, ret, count, slots);
+    GP_LAUNCHED();
+    ring_output_kernel<float><<<sms * 4, 256, smem, st_>>>(g_.n, na, g_.newid, w.y, B_, ret, count, slots);
+    GP_LAUNCHED();
+    ring_complete_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, done_d_, cap_done_, dev_, slots, w.col, w.stat, w.norm,
+                                                      ret, count, block16);
+    GP_LAUNCHED();
+  };
+  retire(*e32_, slots32_, ret32_, cnt_ + 0, 0);
+  if (e16_) retire(*e16_, slots16_, ret16_, cnt_ + 1, 1);
+  // columns past their warm-up move to the 16-bit block (into the buffers each
+  // block's next pass gathers and reads)
+  if (e16_) {
+    const ColumnEngine::View a = e32_->view(), b = e16_->view();
+    ring_migrate_select_kernel<<<1, kRingThreads, 0, st_>>>(dev_, slots32_, a.stat, B_, slots16_, B_, mig_from_,
+                                                            mig_to_);
+    GP_LAUNCHED();
+    const float* fk = a.f[a.pass & 1];
+    const float* fk1 = a.f[(a.pass + 1) & 1];
+    if (b.storage == GP_F16)
+      ring_migrate_columns_kernel<__half><<<sms * 8, 256, 0, st_>>>(na, B_, B_, mig_from_, mig_to_, dev_, fk, fk1, a.y,
+                                                                    (__half*)b.h[b.pass & 1],
+                                                                    (__half*)b.h[(b.pass + 1) & 1], b.y);
+    else
+      ring_migrate_columns_kernel<__nv_bfloat16><<<sms * 8, 256, 0, st_>>>(
+          na, B_, B_, mig_from_, mig_to_, dev_, fk, fk1, a.y, (__nv_bfloat16*)b.h[b.pass & 1],
+          (__nv_bfloat16*)b.h[(b.pass + 1) & 1], b.y);
+    GP_LAUNCHED();
+    ring_migrate_state_kernel<<<B_, 128, 0, st_>>>(mig_from_, mig_to_, dev_, a.col, a.par, a.stat, a.norm, b.col,
+                                                   b.par, b.stat, b.norm);
+    GP_LAUNCHED();
+  }
+  ring_stats_kernel<<<1, 1, 0, st_>>>(ctl_d_, dev_);
+  GP_LAUNCHED();
+}
+
+}  // namespace gp

@@ -159,25 +159,69 @@ __device__ __forceinline__ void stage_indices(const Ctx& c, const TileInfo& t, i
   for (int v = lane; v < nvec; v += 32) cp_async16(idx + 4 * v, src + v, c.pol_stream);
 }
 
-// Kahan-compensated sum of Q_k over the staged indices idx[start + i*stride],
-// i < count, with up to N gathers in flight (hub indices read shared memory).
+// Up to N gathers of Q_k at the staged indices idx[start + (i0 + i)*stride],
+// i < N and i0 + i < count (hub indices read shared memory); slots past count
+// get index -1 and value 0.
 template <int N>
-__device__ __forceinline__ void gather_sum(const Ctx& c, const int* idx, int start, int stride, int count,
-                                           KSum& s) {
+__device__ __forceinline__ void gather_batch(const Ctx& c, const int* idx, int start, int stride, int count, int i0,
+                                             int id[N], float v[N]) {
   const float* q = c.a->qcur;
   const int hub = c.a->hub;
+#pragma unroll
+  for (int i = 0; i < N; ++i) id[i] = i0 + i < count ? idx[start + (i0 + i) * stride] : -1;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    v[i] = id[i] < 0 ? 0.f : id[i] < hub ? c.hub_q[id[i]] : ld_q(q + id[i], c.pol_keep);
+}
+
+// Compensated sum of Q_k over the staged indices idx[start + i*stride],
+// i < count: GP_KAHAN_WAYS Kahan accumulators take the entries in turn (a
+// shorter chain of dependent adds per accumulator) and are merged as float
+// pairs in a fixed order.  With GP_GATHER_PIPE the next batch of N gathers is
+// issued before the current batch is added, so two batches are in flight.
+#ifndef GP_GATHER_PIPE
+#define GP_GATHER_PIPE 0
+#endif
+#ifndef GP_KAHAN_WAYS
+#define GP_KAHAN_WAYS 1
+#endif
+template <int N>
+__device__ __forceinline__ DF gather_sum(const Ctx& c, const int* idx, int start, int stride, int count) {
+  constexpr int W = GP_KAHAN_WAYS;
+  KSum s[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) s[w] = KSum{0.f, 0.f};
+#if GP_GATHER_PIPE
+  int id[N];
+  float v[N];
+  gather_batch<N>(c, idx, start, stride, count, 0, id, v);
+  for (int i0 = 0; i0 < count; i0 += N) {
+    int cid[N];
+    float cv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      cid[i] = id[i];
+      cv[i] = v[i];
+    }
+    if (i0 + N < count) gather_batch<N>(c, idx, start, stride, count, i0 + N, id, v);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (cid[i] >= 0) ksum_add(s[i % W], cv[i]);
+  }
+#else
   for (int i0 = 0; i0 < count; i0 += N) {
     int id[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) id[i] = i0 + i < count ? idx[start + (i0 + i) * stride] : -1;
     float v[N];
+    gather_batch<N>(c, idx, start, stride, count, i0, id, v);
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      v[i] = id[i] < 0 ? 0.f : id[i] < hub ? c.hub_q[id[i]] : ld_q(q + id[i], c.pol_keep);
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-      if (id[i] >= 0) ksum_add(s, v[i]);
+      if (id[i] >= 0) ksum_add(s[i % W], v[i]);
   }
+#endif
+  DF r = ksum_value(s[0]);
+#pragma unroll
+  for (int w = 1; w < W; ++w) r = df_add(r, ksum_value(s[w]));
+  return r;
 }
 
 // Rows tile.  With nrows >= 32 (degree <= kTileCap/32) the warp gathers the
@@ -239,9 +283,9 @@ __device__ __forceinline__ void finish_rows(Ctx& c, const TileInfo& t, int* idx)
       if (a.cheb) qp = ld_own(a.qprev + t.row0 + r);
       yv = ld_own2(a.y + t.row0 + r);
     }
-    KSum s{0.f, 0.f};
-    if (own) gather_sum<GP_GATHER_N>(c, idx, off0 + r * t.d + sub, G, (t.d - sub + G - 1) / G, s);
-    const DF v = shfl_sum_df(ksum_value(s), G);
+    DF sv{0.f, 0.f};
+    if (own) sv = gather_sum<GP_GATHER_N>(c, idx, off0 + r * t.d + sub, G, (t.d - sub + G - 1) / G);
+    const DF v = shfl_sum_df(sv, G);
     if (own && sub == 0) row_update(c, t.row0 + r, t.d, v, qp, yv);
   }
 }
@@ -251,9 +295,7 @@ __device__ __forceinline__ void finish_chunk(Ctx& c, const TileInfo& t, const in
   const StepArgs& a = *c.a;
   const int lane = threadIdx.x & 31;
   const int off0 = (int)(t.e0 & 3);
-  KSum s{0.f, 0.f};
-  gather_sum<GP_GATHER_N>(c, idx, off0 + lane, 32, (t.len - lane + 31) / 32, s);
-  const DF v = shfl_sum_df(ksum_value(s), 32);
+  const DF v = shfl_sum_df(gather_sum<GP_GATHER_N>(c, idx, off0 + lane, 32, (t.len - lane + 31) / 32), 32);
   if (lane == 0) a.part[a.poff[t.row0] + t.p] = make_float2(v.hi, v.lo);
 }
 
