@@ -183,11 +183,11 @@ struct Serve {
   void complete(const RingDone& rd) {
     InFlight f;
     {
+      // the ticket stays in flight (gp_poll: GP_EAGAIN) until its result is done
       std::lock_guard<std::mutex> lk(mu);
       auto it = inflight.find(rd.ticket);
       if (it == inflight.end()) return;
-      f = std::move(it->second);
-      inflight.erase(it);
+      f = it->second;
     }
     if (f.staging >= 0) {
       const size_t esz = f.req.out_dtype == GP_F64 ? 8 : 4;
@@ -195,6 +195,7 @@ struct Serve {
       GP_CUDA_TRY(cudaStreamSynchronize(copy_stream));
     }
     std::lock_guard<std::mutex> lk(mu);
+    inflight.erase(rd.ticket);
     if (f.staging >= 0) staging_free.push_back(f.staging);
     Done d{GP_OK, {}};
     d.info.K = rd.K;
