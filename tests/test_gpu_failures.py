@@ -107,8 +107,8 @@ def test_allocator_null_at_graph_create(gp):
 
 
 def test_allocator_null_inside_the_running_service(gp):
-    """The service allocates its host-output staging buffer when the first
-    request with a host output finishes.  With the allocator failing by then,
+    """The service allocates a host-output staging buffer when it first hands
+    a request with a host output to the device.  With the allocator failing by then,
     the service loop stops, every ticket queued or in flight completes with
     GP_ENOMEM, later submissions are refused, and destroy still returns and
     frees everything."""
@@ -126,8 +126,8 @@ def test_allocator_null_inside_the_running_service(gp):
             assert info["K"] > 0
         fa.budget = 0  # every allocation from now on fails
         host = np.empty(g.n, dtype=np.float64)
-        tickets = [gp.gp_submit(dg, gp.make_request(1, srcs[4], 5.0, 1e-6, host))]
-        tickets += [gp.gp_submit(dg, gp.make_request(0, s, 0.1, 1e-6, ys[i])) for i, s in enumerate(srcs[5:])]
+        tickets = [gp.gp_submit(dg, gp.make_request(0, s, 0.1, 1e-6, ys[i])) for i, s in enumerate(srcs[5:])]
+        tickets.append(gp.gp_submit(dg, gp.make_request(1, srcs[4], 5.0, 1e-6, host)))
         statuses = []
         for t in tickets:
             try:
@@ -138,7 +138,7 @@ def test_allocator_null_inside_the_running_service(gp):
         assert fa.failed >= 1
         # the host-output ticket and whatever was still queued or running fail; the
         # rest may have finished before the failure
-        assert statuses[0] == gp.GP_ENOMEM, statuses
+        assert statuses[-1] == gp.GP_ENOMEM, statuses
         assert all(st in (gp.GP_OK, gp.GP_ENOMEM) for st in statuses), statuses
         with pytest.raises(gp.GPError):
             gp.gp_submit(dg, gp.make_request(0, srcs[0], 0.2, 1e-6, ys[0]))
