@@ -205,11 +205,18 @@ __global__ void ring_output_kernel(int64_t n, int64_t na, const int32_t* newid, 
   extern __shared__ __align__(16) float s_tile[];  // 32 x B
   __shared__ int64_t s_row[32];
   __shared__ int s_any;
+  __shared__ int s_grp[kRingThreads / 4];  // 4-column groups holding a column to write
   constexpr int kF64 = sizeof(OUT) == 8;
   if (threadIdx.x == 0) s_any = 0;
+  for (int q = threadIdx.x; q < kRingThreads / 4; q += blockDim.x) s_grp[q] = 0;
   __syncthreads();
-  for (int t = threadIdx.x; t < nc; t += blockDim.x)
-    if (slots[ret_list[t]].out_f64 == kF64) s_any = 1;
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    const int j = ret_list[t];
+    if (slots[j].out_f64 == kF64) {
+      s_any = 1;
+      s_grp[j >> 2] = 1;
+    }
+  }
   __syncthreads();
   if (!s_any) return;  // no retired column wants this output type
   for (int64_t u0 = (int64_t)blockIdx.x * 32; u0 < n; u0 += (int64_t)gridDim.x * 32) {
@@ -221,6 +228,7 @@ __global__ void ring_output_kernel(int64_t n, int64_t na, const int32_t* newid, 
     const int nvec = 32 * (B / 4);
     for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
       const int r = v / (B / 4), c4 = v % (B / 4);
+      if (!s_grp[c4]) continue;  // only the groups of the columns written below
       const int64_t i = s_row[r];
       const float4 val = (i >= 0 && i < na) ? *reinterpret_cast<const float4*>(y + i * B + 4 * c4)
                                             : make_float4(0.f, 0.f, 0.f, 0.f);
