@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--serve-width", type=int, default=256,
                    help="chunglu24_serve: query slots of the service block (a power of two, <= 512)")
     p.add_argument("--loads", default="0.5,0.8,0.95", help="chunglu24_serve: offered load levels")
+    p.add_argument("--serve-storage", default="fp32", choices=["fp32", "bf16", "fp16"],
+                   help="chunglu24_serve: storage of the service's blocks")
     return p.parse_args()
 
 
@@ -432,20 +434,7 @@ def oracle_leg(g, queries, tol, seconds, captured, single_K):
                      f"in {dt:.1f} s, FP64 CPU oracle, OpenMP over rows",
            "one_thread": {"value": done1 / dt1, "unit": UNIT, "cores": 1,
                           "sample": f"first {done1} queries in {dt1:.1f} s on one thread"}}
-    errors = {}
-    sample = sorted({i for form in captured.values() for i in form["y"]})
-    ystar = {}
-    for i in sample:
-        fn, s, p = queries[i]
-        ystar[i], _, _ = O.chebypower_tol(g, s, "ppr" if fn == 0 else "hkpr", p, 1e-12)
-    for name, form in captured.items():
-        rows = []
-        for i, y in sorted(form["y"].items()):
-            d = y - ystar[i]
-            t = form["tol"][i] if isinstance(form["tol"], dict) else form["tol"]
-            rows.append({"query": i, "l1": float(np.abs(d).sum()), "maxabs": float(np.abs(d).max()), "l1_tol": t})
-        errors[name] = {"l1_max": max(r["l1"] for r in rows), "maxabs_max": max(r["maxabs"] for r in rows),
-                        "within_tol": all(r["l1"] <= r["l1_tol"] for r in rows), "queries": rows}
+    errors = oracle_errors(g, queries, captured)
     if "single" in captured and single_K:
         rows = []
         for i, y in sorted(captured["single"]["y"].items()):
@@ -456,9 +445,30 @@ def oracle_leg(g, queries, tol, seconds, captured, single_K):
         errors["single"]["same_K"] = {"l1_max": max(r["l1"] for r in rows),
                                       "maxabs_max": max(r["maxabs"] for r in rows), "bar": "l1 <= 1e-6, max-abs <= 1e-8",
                                       "queries": rows}
-    errors["reference"] = "FP64 oracle ChebyPower to l1 1e-12 (converged y*), queries " + \
-        ", ".join(f"{i}: {'SSPPR' if queries[i][0] == 0 else 'HKPR'} s={queries[i][1]}" for i in sample)
     return cpu, errors
+
+
+def oracle_errors(g, queries, captured, ref_tol=1e-12):
+    """l1 and max-abs of each captured output against the oracle's converged
+    vector y* = f(P) e_s (ChebyPower to l1 ref_tol), per result."""
+    import oracle as O
+    errors = {}
+    sample = sorted({i for form in captured.values() for i in form["y"]})
+    ystar = {}
+    for i in sample:
+        fn, s, p = queries[i]
+        ystar[i], _, _ = O.chebypower_tol(g, s, "ppr" if fn == 0 else "hkpr", p, ref_tol)
+    for name, form in captured.items():
+        rows = []
+        for i, y in sorted(form["y"].items()):
+            d = y - ystar[i]
+            t = form["tol"][i] if isinstance(form["tol"], dict) else form["tol"]
+            rows.append({"query": i, "l1": float(np.abs(d).sum()), "maxabs": float(np.abs(d).max()), "l1_tol": t})
+        errors[name] = {"l1_max": max(r["l1"] for r in rows), "maxabs_max": max(r["maxabs"] for r in rows),
+                        "within_tol": all(r["l1"] <= r["l1_tol"] for r in rows), "queries": rows}
+    errors["reference"] = f"FP64 oracle ChebyPower to l1 {ref_tol:g} (converged y*), queries " + \
+        ", ".join(f"{i}: {'SSPPR' if queries[i][0] == 0 else 'HKPR'} s={queries[i][1]}" for i in sample)
+    return errors
 
 
 def run_reference(args, rank, world):
@@ -671,8 +681,9 @@ def mixed_queries(srcs, seed):
     return [(MIXED_FUNCTIONS[i % 6][0], int(s), MIXED_FUNCTIONS[i % 6][1]) for i, s in enumerate(srcs)]
 
 
-def batched_forms(gp, g, queries, forms, width, reps, dev):
-    """gp_batch over `queries` for each (name, storage, tol): queries/s, K range, footprint."""
+def batched_forms(gp, g, queries, forms, width, reps, dev, sample=(), captured=None):
+    """gp_batch over `queries` for each (name, storage, tol): queries/s, K range,
+    footprint; the outputs of the `sample` queries go to `captured`."""
     import torch
     out = {}
     for name, storage, tol in forms:
@@ -694,6 +705,8 @@ def batched_forms(gp, g, queries, forms, width, reps, dev):
                      "K_min": min(ks), "K_max": max(ks), "mean_K": float(np.mean(ks)),
                      "k16_from": int(min(i["k16_from"] for i in infos)),
                      "block_bytes": int(used)}
+        if captured is not None:
+            captured[name] = {"tol": tol, "y": {i: _host(ys[i % len(ys)]) for i in sample}}
         dg.close()
         del ys
     return out
@@ -713,11 +726,16 @@ def serve_poisson(gp, g, dev, args):
     params = [(0.1, 0.2, 0.5)[k] if f == 0 else (3.0, 5.0, 10.0)[k] for f, k in zip(fns, rng.integers(0, 3, nreq))]
     tols = rng.choice([1e-4, 1e-5, 1e-6], nreq)
     specs = [(int(f), int(s), float(p), float(t)) for f, s, p, t in zip(fns, srcs, params, tols)]
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=args.serve_width)
+    st = {"fp32": gp.GP_F32, "bf16": gp.GP_BF16, "fp16": gp.GP_F16}[args.serve_storage]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=args.serve_width, storage=st)
     pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range(args.serve_width + 64)]
-    res, _ = serve_levels(gp, dg, specs, pool, [float(x) for x in args.loads.split(",")], 5)
+    sample = list(range(min(args.cpu_sample, nreq)))
+    res, kept = serve_levels(gp, dg, specs, pool, [float(x) for x in args.loads.split(",")], 5, keep=sample)
+    res["storage"] = args.serve_storage
     dg.close()
-    return res
+    queries = [(f, s, p) for f, s, p, _ in specs]
+    captured = {"serving": {"tol": {i: specs[i][3] for i in sample}, "y": {i: _host(kept[i]) for i in sample}}}
+    return res, queries, captured
 
 
 def propagate_forms(gp, g, dev, reps):
@@ -827,12 +845,18 @@ def run_workload(args, rank, world):
         value, metric = res["bf16_tol1e-4"]["value"], "feature columns/s, Z = f(D^-a A D^-b) X (rmat22_propagate)"
         queries = [None] * 128
     elif queries is not None:
-        res = batched_forms(gp, g, queries, forms, width, args.batch_reps, dev)
+        captured = {}
+        res = batched_forms(gp, g, queries, forms, width, args.batch_reps, dev, sample=range(min(args.cpu_sample, 6)),
+                            captured=captured)
         value, metric = res[headline]["value"], f"batched queries/s at l1<={forms[0][2]:g} ({args.workload})"
     else:
-        res = serve_poisson(gp, g, dev, args)
+        res, queries, captured = serve_poisson(gp, g, dev, args)
         value, metric = res["saturated"]["value"], "served queries/s, p50/p99 latency (chunglu24_serve)"
     clocks = sampler.stop()
+    # the sampled outputs against the oracle's converged vectors (CPU leg, rank 0, N = 1)
+    errors = None
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload not in ("rmat22_propagate", "rmat22_push"):
+        errors = oracle_errors(g, queries, captured, ref_tol=1e-10)
     if rank == 0:
         print(json.dumps({
             "metric": metric, "value": value,
@@ -843,7 +867,7 @@ def run_workload(args, rank, world):
             "config": {"workload": args.workload, "graph": g.name, "n": g.n, "nnz": g.nnz,
                        "queries": len(queries) if queries else args.requests, "block_width": width,
                        "generate_s": round(t_gen, 1), "parallelism": "replicas"},
-            "forms": res, "clocks": clocks}), flush=True)
+            "forms": res, "errors_vs_oracle": errors, "clocks": clocks}), flush=True)
 
 
 def main():
