@@ -195,54 +195,40 @@ __global__ void __launch_bounds__(kRingThreads) ring_retire_kernel(const RingCtl
 }
 
 // y of the retired columns (relabelled rows) into their outputs in the
-// caller's numbering, for the columns whose output type is OUT: a CTA copies
-// 32 rows of y into shared memory, then writes each column's 32 values.
+// caller's numbering, for the columns whose output type is OUT: a thread per
+// caller row u reads its relabelled row's values of those columns (the same
+// row, so the columns share cached sectors) and writes them coalesced across
+// the warp; rows of isolated nodes get 0.
 template <typename OUT>
 __global__ void ring_output_kernel(int64_t n, int64_t na, const int32_t* newid, const float* y, int B,
                                    const int* ret_list, const int* ret_count, const SlotDev* slots) {
   const int nc = *ret_count;
   if (nc == 0) return;
-  extern __shared__ __align__(16) float s_tile[];  // 32 x B
-  __shared__ int64_t s_row[32];
-  __shared__ int s_any;
-  __shared__ int s_grp[kRingThreads / 4];  // 4-column groups holding a column to write
+  __shared__ int s_col[kRingThreads];
+  __shared__ OUT* s_out[kRingThreads];
+  __shared__ int s_m;
   constexpr int kF64 = sizeof(OUT) == 8;
-  if (threadIdx.x == 0) s_any = 0;
-  for (int q = threadIdx.x; q < kRingThreads / 4; q += blockDim.x) s_grp[q] = 0;
+  if (threadIdx.x == 0) s_m = 0;
   __syncthreads();
   for (int t = threadIdx.x; t < nc; t += blockDim.x) {
     const int j = ret_list[t];
     if (slots[j].out_f64 == kF64) {
-      s_any = 1;
-      s_grp[j >> 2] = 1;
+      const int at = atomicAdd(&s_m, 1);
+      s_col[at] = j;
+      s_out[at] = static_cast<OUT*>(slots[j].out);
     }
   }
   __syncthreads();
-  if (!s_any) return;  // no retired column wants this output type
-  for (int64_t u0 = (int64_t)blockIdx.x * 32; u0 < n; u0 += (int64_t)gridDim.x * 32) {
-    if (threadIdx.x < 32) {
-      const int64_t u = u0 + threadIdx.x;
-      s_row[threadIdx.x] = u < n ? (int64_t)newid[u] : -1;
+  const int m = s_m;
+  if (m == 0) return;  // no retired column wants this output type
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = newid[u];
+    if (i >= na) {
+      for (int t = 0; t < m; ++t) s_out[t][u] = (OUT)0;
+    } else {
+      const float* row = y + i * B;
+      for (int t = 0; t < m; ++t) s_out[t][u] = (OUT)__ldg(row + s_col[t]);
     }
-    __syncthreads();
-    const int nvec = 32 * (B / 4);
-    for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-      const int r = v / (B / 4), c4 = v % (B / 4);
-      if (!s_grp[c4]) continue;  // only the groups of the columns written below
-      const int64_t i = s_row[r];
-      const float4 val = (i >= 0 && i < na) ? *reinterpret_cast<const float4*>(y + i * B + 4 * c4)
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-      *reinterpret_cast<float4*>(s_tile + r * B + 4 * c4) = val;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t u = u0 + lane;
-    for (int t = warp; t < nc; t += nw) {
-      const int j = ret_list[t];
-      if (slots[j].out_f64 != kF64) continue;
-      if (u < n) static_cast<OUT*>(slots[j].out)[u] = (OUT)s_tile[lane * B + j];
-    }
-    __syncthreads();
   }
 }
 
@@ -498,14 +484,13 @@ void RingLoop::iterate() {
     e16_->pass_device(cnt_ + 3, &dev_->active16);
   }
   // retirement: outputs, done records, freed columns
-  const size_t smem = sizeof(float) * 32 * B_;
   auto retire = [&](ColumnEngine& e, SlotDev* slots, int* ret, int* count, int block16) {
     const ColumnEngine::View w = e.view();
     ring_retire_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, dev_, cap_done_, slots, w.stat, B_, ret, count);
     GP_LAUNCHED();
-    ring_output_kernel<double><<<sms * 4, 256, smem, st_>>>(g_.n, na, g_.newid, w.y, B_, ret, count, slots);
+    ring_output_kernel<double><<<sms * 8, 256, 0, st_>>>(g_.n, na, g_.newid, w.y, B_, ret, count, slots);
     GP_LAUNCHED();
-    ring_output_kernel<float><<<sms * 4, 256, smem, st_>>>(g_.n, na, g_.newid, w.y, B_, ret, count, slots);
+    ring_output_kernel<float><<<sms * 8, 256, 0, st_>>>(g_.n, na, g_.newid, w.y, B_, ret, count, slots);
     GP_LAUNCHED();
     ring_complete_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, done_d_, cap_done_, dev_, slots, w.col, w.stat, w.norm,
                                                       ret, count, block16);
