@@ -75,7 +75,7 @@ def parse():
                         "served forms on the larger graphs")
     p.add_argument("--requests", type=int, default=10000, help="chunglu24_serve: requests per load level")
     p.add_argument("--serve-width", type=int, default=256,
-                   help="chunglu24_serve: query slots of the service block (a power of two, <= 512)")
+                   help="query slots of the service block (a power of two, <= 512)")
     p.add_argument("--loads", default="0.5,0.8,0.95", help="chunglu24_serve: offered load levels")
     p.add_argument("--serve-storage", default="fp32", choices=["fp32", "bf16", "fp16"],
                    help="chunglu24_serve: storage of the service's blocks")
@@ -234,14 +234,13 @@ def serve_levels(gp, dg, specs, pool, loads, seed, keep=()):
 
 
 def bench_serving(gp, g, queries, dev, world, nreq=1024, loads=(0.5, 0.8, 0.95), sample=(), storage="fp32",
-                  tols=(1e-4, 1e-5, 1e-6), name="serving"):
+                  tols=(1e-4, 1e-5, 1e-6), name="serving", width=256):
     """The step's queries through gp_submit/gp_poll (continuous batching), l1
     tolerances cycling over `tols`: the saturated rate, then Poisson arrivals
     at 50/80/95% of it, with p50/p99 latency (arrival to completion).  With
     16-bit storage the service starts each column in FP32 and moves it to a
     16-bit block after its own warm-up."""
     import torch
-    width = 256
     st = {"fp32": gp.GP_F32, "bf16": gp.GP_BF16, "fp16": gp.GP_F16}[storage]
     dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=width, storage=st)
     specs = [queries[i % len(queries)] + (tols[i % len(tols)],) for i in range(nreq)]
@@ -632,11 +631,12 @@ def run_ours(args, rank, world):
         for name, storage, tols in (("serving", "fp32", (1e-4, 1e-5, 1e-6)),
                                     ("serving_bf16", "bf16", (1e-4, 1e-5, 1e-6)),
                                     ("serving_fp32_tol1e-4", "fp32", (1e-4,)),
-                                    ("serving_bf16_tol1e-4", "bf16", (1e-4,))):
+                                    ("serving_bf16_tol1e-4", "bf16", (1e-4,)),
+                                    ("serving_fp16_tol1e-4", "fp16", (1e-4,))):
             if name not in legs:
                 continue
             serving[name], outs = bench_serving(gp, g, queries, dev, world, nreq=args.serve_requests, sample=sample,
-                                                storage=storage, tols=tols, name=name)
+                                                storage=storage, tols=tols, name=name, width=args.serve_width)
             captured.update(outs)
         single4 = (batched or {}).get("bf16_tol1e-4", {}).get("single_source_same_tol")
         if single4 and "serving_bf16_tol1e-4" in serving:
