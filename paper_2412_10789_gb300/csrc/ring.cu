@@ -333,10 +333,10 @@ __global__ void ring_migrate_columns_kernel(int64_t na, int ldb_s, int ldb_d, co
 
 // The moved columns' coefficients, state and last norm (a block per column);
 // the FP32 column is cleared.
-__global__ void ring_migrate_state_kernel(const int* from, const int* to, const RingDev* dev, ColState* cs_s,
+__global__ void ring_migrate_state_kernel(const int* from, const int* to, const int* count, ColState* cs_s,
                                           const ColParam* cp_s, ColStat* st_s, float* nm_s, ColState* cs_d,
                                           ColParam* cp_d, ColStat* st_d, float* nm_d) {
-  if ((int)blockIdx.x >= dev->mig_count) return;
+  if ((int)blockIdx.x >= *count) return;
   const int a = from[blockIdx.x], b = to[blockIdx.x];
   const float* src = reinterpret_cast<const float*>(cp_s + a);
   float* dst = reinterpret_cast<float*>(cp_d + b);
@@ -349,6 +349,65 @@ __global__ void ring_migrate_state_kernel(const int* from, const int* to, const 
     cs_s[a] = ColState{0, 0.f};
     st_s[a] = ColStat{0, 0, 0, 0.f};
     nm_s[a] = 0.f;
+  }
+}
+
+// Pack a block's busy columns below the smallest power of two (at least
+// min_w) that holds them all, once no request waits in the ring, so that the
+// passes of a lightly loaded block narrow again (the width follows the highest
+// busy slot).  Columns above that width move into free slots below it; their
+// slot records move here, their data and state by the two kernels below.
+__global__ void __launch_bounds__(kRingThreads) ring_compact_select_kernel(const RingCtl* ctl, const RingDev* dev,
+                                                                           SlotDev* slots, int B, int min_w,
+                                                                           int* from, int* to, int* count) {
+  __shared__ int s_scan[kRingThreads];
+  __shared__ int s_from[kRingThreads];
+  __shared__ int s_to[kRingThreads];
+  __shared__ int s_quiet;
+  const int j = threadIdx.x;
+  if (j == 0) s_quiet = load_acquire_sys(&ctl->tail) == dev->head;
+  const int busy = j < B && slots[j].busy;
+  int nb = 0;
+  (void)block_rank(busy, s_scan, &nb);
+  int w = min_w;
+  while (w < nb) w <<= 1;
+  w = std::min(w, B);
+  const int mover = busy && j >= w;
+  int nm = 0;
+  const int rm = block_rank(mover, s_scan, &nm);
+  if (mover) s_from[rm] = j;
+  const int hole = j < w && !busy;
+  int nh = 0;
+  const int rh = block_rank(hole, s_scan, &nh);
+  if (hole) s_to[rh] = j;
+  __syncthreads();
+  const int take = s_quiet ? std::min(nm, nh) : 0;
+  if (j < take) {
+    const int a = s_from[j], b = s_to[j];
+    slots[b] = slots[a];
+    slots[a].busy = 0;
+    from[j] = a;
+    to[j] = b;
+  }
+  if (j == 0) *count = take;
+}
+
+// Column `from[t]` of every row copied to column `to[t]` of the same block
+// (the stored pair and y), a warp per row.
+template <typename T>
+__global__ void ring_move_columns_kernel(int64_t na, int B, const int* from, const int* to, const int* count, T* a0,
+                                         T* a1, float* y) {
+  const int nc = *count;
+  if (nc == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
+    for (int t = lane; t < nc; t += 32) {
+      const int64_t a = r * B + from[t], b = r * B + to[t];
+      a0[b] = a0[a];
+      a1[b] = a1[a];
+      y[b] = y[a];
+    }
   }
 }
 
@@ -397,7 +456,7 @@ RingLoop::RingLoop(Graph& g, int width, gp_dtype storage, cudaStream_t st) : g_(
     mapped_alloc(&ctl_, &ctl_d_, 1);
     mapped_alloc(&req_, &req_d_, (size_t)cap_req_);
     mapped_alloc(&done_, &done_d_, (size_t)cap_done_);
-    const size_t bytes = sizeof(RingDev) + 2 * kRingThreads * sizeof(SlotDev) + (5 * kRingThreads + 4) * sizeof(int);
+    const size_t bytes = sizeof(RingDev) + 2 * kRingThreads * sizeof(SlotDev) + (5 * kRingThreads + 8) * sizeof(int);
     dmem_ = g.alloc.get(bytes);
     GP_CUDA_TRY(cudaMemsetAsync(dmem_, 0, bytes, st_));
     GP_CUDA_TRY(cudaStreamSynchronize(st_));
@@ -516,10 +575,29 @@ void RingLoop::iterate() {
           na, B_, B_, mig_from_, mig_to_, dev_, fk, fk1, a.y, (__nv_bfloat16*)b.h[b.pass & 1],
           (__nv_bfloat16*)b.h[(b.pass + 1) & 1], b.y);
     GP_LAUNCHED();
-    ring_migrate_state_kernel<<<B_, 128, 0, st_>>>(mig_from_, mig_to_, dev_, a.col, a.par, a.stat, a.norm, b.col,
-                                                   b.par, b.stat, b.norm);
+    ring_migrate_state_kernel<<<B_, 128, 0, st_>>>(mig_from_, mig_to_, &dev_->mig_count, a.col, a.par, a.stat,
+                                                   a.norm, b.col, b.par, b.stat, b.norm);
     GP_LAUNCHED();
   }
+  // a lightly loaded block packs its columns so that its passes narrow
+  auto compact = [&](ColumnEngine& e, SlotDev* slots) {
+    const ColumnEngine::View w = e.view();
+    ring_compact_select_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, dev_, slots, B_, e.min_width(), mig_from_,
+                                                            mig_to_, cnt_ + 4);
+    GP_LAUNCHED();
+    if (w.pure16)
+      ring_move_columns_kernel<uint16_t><<<sms * 8, 256, 0, st_>>>(na, B_, mig_from_, mig_to_, cnt_ + 4,
+                                                                   (uint16_t*)w.h[0], (uint16_t*)w.h[1], w.y);
+    else
+      ring_move_columns_kernel<float><<<sms * 8, 256, 0, st_>>>(na, B_, mig_from_, mig_to_, cnt_ + 4, w.f[0],
+                                                                w.f[1], w.y);
+    GP_LAUNCHED();
+    ring_migrate_state_kernel<<<B_, 128, 0, st_>>>(mig_from_, mig_to_, cnt_ + 4, w.col, w.par, w.stat, w.norm, w.col,
+                                                   w.par, w.stat, w.norm);
+    GP_LAUNCHED();
+  };
+  compact(*e32_, slots32_);
+  if (e16_) compact(*e16_, slots16_);
   ring_stats_kernel<<<1, 1, 0, st_>>>(ctl_d_, dev_);
   GP_LAUNCHED();
 }

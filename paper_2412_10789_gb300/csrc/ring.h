@@ -107,7 +107,8 @@ class RingLoop {
   int* new_list_ = nullptr;
   int* ret32_ = nullptr;
   int* ret16_ = nullptr;
-  int* cnt_ = nullptr;          // [0] retired FP32, [1] retired 16-bit, [2] width FP32, [3] width 16-bit
+  int* cnt_ = nullptr;          // [0] retired FP32, [1] retired 16-bit, [2] width FP32, [3] width 16-bit,
+                                // [4] columns moved by the compaction
   int* mig_from_ = nullptr;
   int* mig_to_ = nullptr;
   uint64_t tail_ = 0;           // requests published
