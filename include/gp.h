@@ -289,9 +289,12 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
  * a power of two; a block wider than 256 columns runs as 256-column halves,
  * each with its own pass.  With cfg.storage GP_BF16 or GP_F16 a second block of
  * the same width stores 16 bits: every request starts in the FP32 block and
- * moves to the 16-bit block once its own warm-up is over (see warmup_tail;
- * info.k16_from reports the first term stored in 16 bits, K + 1 if none); with
- * GP_F32 the service stores FP32 only.  The request's y_out must stay valid
+ * moves to the 16-bit block once its own warm-up is over (see warmup_tail)
+ * if at least six more steps are certain to follow (info.k16_from reports the
+ * first term stored in 16 bits, K + 1 if none); with GP_F32 the service stores
+ * FP32 only.  Admission, retirement, outputs and slot refills are decided on
+ * the device every pass (a request loop in mapped host memory), and a lightly
+ * loaded block packs its columns so that its passes narrow.  The request's y_out must stay valid
  * until gp_poll reports completion.
  * gp_poll returns GP_OK (and fills info) once the ticket is done, GP_EAGAIN
  * before that, GP_ENOTFOUND for an unknown or already-collected ticket.

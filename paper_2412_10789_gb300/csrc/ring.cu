@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(kRingThreads) ring_admit_kernel(RingCtl* ctl, 
     sd.out_f64 = r.out_f64;
     sd.warm = r.param.warm;
     sd.k16 = -1;
+    sd.k_low = r.k_low;
+    sd.pad = 0;
     slots[j] = sd;
     col[j] = ColState{1, 0.f};
     stat[j] = ColStat{1, 0, 0, 1.0f};
@@ -270,7 +272,10 @@ __global__ void __launch_bounds__(kRingThreads) ring_complete_kernel(RingCtl* ct
 
 // FP32 columns past their own warm-up (newest term Q_k with k >= warm + 3, so
 // every 16-bit term has index >= warm + 2) paired with free 16-bit slots; the
-// slot records move with them.
+// slot records move with them.  A column moves only while at least
+// kMinSteps16 steps are certain to remain (k_low - k): moving costs a copy of
+// its rows, which a few cheaper 16-bit steps do not repay.
+constexpr int kMinSteps16 = 6;
 __global__ void __launch_bounds__(kRingThreads) ring_migrate_select_kernel(RingDev* dev, SlotDev* s32,
                                                                            const ColStat* st32, int B32, SlotDev* s16,
                                                                            int B16, int* from, int* to) {
@@ -278,7 +283,8 @@ __global__ void __launch_bounds__(kRingThreads) ring_migrate_select_kernel(RingD
   __shared__ int s_from[kRingThreads];
   __shared__ int s_to[kRingThreads];
   const int j = threadIdx.x;
-  const int cand = j < B32 && s32[j].busy && !st32[j].done && st32[j].k >= s32[j].warm + 3;
+  const int cand = j < B32 && s32[j].busy && !st32[j].done && st32[j].k >= s32[j].warm + 3 &&
+                   s32[j].k_low - st32[j].k >= kMinSteps16;
   int ncand = 0;
   const int rc = block_rank(cand, s_scan, &ncand);
   if (cand) s_from[rc] = j;

@@ -29,7 +29,7 @@ struct RingReq {
   void* out;      // device output: the caller's buffer or a staging buffer
   int64_t src;    // relabelled source (degree >= 1)
   int out_f64;    // 1: double output, 0: float
-  int pad;
+  int k_low;      // no stop before this step (the stop rule with max ||r_l||_1 at its least, 1)
 };
 
 struct RingDone {
@@ -48,7 +48,9 @@ struct SlotDev {
   int busy;
   int out_f64;
   int warm;
-  int k16;  // first 16-bit term once migrated, else -1
+  int k16;    // first 16-bit term once migrated, else -1
+  int k_low;  // no stop before this step
+  int pad;
 };
 
 // Device counters of the loop.

@@ -313,6 +313,10 @@ void prepare(const Graph& g, gp_dtype storage, Ticket& t) {
                   : r.k_rule == GP_K_PAPER ? std::min(kcap - 1, paper_k(r.function, r.param, r.l1_tol))
                                            : 0;
   q.param.warm = storage == GP_F32 ? kcap : warm_step(c, kcap, column_warm_tail(g.cfg.warmup_tail, storage, r.l1_tol));
+  // with max ||r_l||_1 >= ||r_0||_1 = 1 the tail rule cannot stop before k_lower(.., 1)
+  q.k_low = r.k_rule == GP_K_TAIL   ? k_lower(tail, r.l1_tol / kCMargin, 1.0)
+            : q.param.kstop > 0 ? q.param.kstop
+                                : kcap;
   q.ticket = t.id;
   q.src = g.h_newid[r.source];
   q.out_f64 = r.out_dtype == GP_F64 ? 1 : 0;

@@ -224,7 +224,8 @@ def test_serving_matches_oracle_and_alone(gp, storage):
     """Continuous batching: 48 mixed requests through a 16-slot service, each
     within its tolerance of the oracle and the same alone as in the mix.  With
     16-bit storage the columns start in the FP32 block and move to the 16-bit
-    block after their own warm-up (k16_from <= K reports it)."""
+    block after their own warm-up when enough steps remain (k16_from <= K
+    reports it)."""
     g = graph("rmat14")
     srcs = gg.sources(g, 48, 19)
     dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16,
@@ -243,8 +244,8 @@ def test_serving_matches_oracle_and_alone(gp, storage):
         moved = sum(1 for i, inf in enumerate(infos) if inf["k16_from"] <= inf["K"])
         if storage == "f32":
             assert moved == 0
-        else:  # every 1e-4 request outlives its warm-up on this graph
-            assert moved >= len(srcs) // 3, [(inf["K"], inf["k16_from"]) for inf in infos]
+        else:  # the columns with at least six steps certain to remain after their warm-up
+            assert moved >= len(srcs) // 8, [(inf["K"], inf["k16_from"]) for inf in infos]
         for i, s in enumerate(srcs):
             fn, p = MIX[i % len(MIX)]
             tol = [1e-4, 1e-5, 1e-6][i % 3]
