@@ -66,7 +66,7 @@ def parse():
                    help="rmat22 serving leg: requests per arrival pattern")
     p.add_argument("--cpu-sample", type=int, default=4,
                    help="queries whose GPU outputs are checked against the converged FP64 oracle")
-    p.add_argument("--batch-storage", default="bf16,fp16,fp32", help="storages of the batched form")
+    p.add_argument("--batch-storage", default="bf16,fp16,fp32,fp32_1e-4", help="storages of the batched form")
     p.add_argument("--batch-reps", type=int, default=3)
     p.add_argument("--workload", default="rmat22",
                    choices=["rmat22", "rmat24_mixed", "chunglu24_serve", "rmat26_int64", "rmat22_propagate",

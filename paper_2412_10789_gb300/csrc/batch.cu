@@ -917,10 +917,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
 
 // Before each pass: fold the last pass's norm into each active column's
 // running max, apply its stop rule, and set the coefficient of the next step.
+// phase -1 treats every column (before a pass); the service splits it: phase
+// 0 before a pass treats only columns that have not run one (k = 1), phase 1
+// right after the pass treats the others, so a column whose rule fires on the
+// norm of that pass retires before the next pass instead of riding it idle.
 __global__ void control_kernel(ColState* col, const ColParam* par, ColStat* stat, float* norm, int B, int kcap,
-                               int* tile_ctr) {
+                               int* tile_ctr, int phase) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j == 0) *tile_ctr = 0;
+  if (j == 0 && phase <= 0) *tile_ctr = 0;
   if (j >= B) return;
   ColState& cs = col[j];
   const ColParam& p = par[j];
@@ -929,6 +933,7 @@ __global__ void control_kernel(ColState* col, const ColParam* par, ColStat* stat
     norm[j] = 0.f;
     return;
   }
+  if ((phase == 0 && st.k != 1) || (phase == 1 && st.k < 2)) return;
   if (st.k > 1) st.C = fmaxf(st.C, norm[j]);  // ||r_k||_1 from the last pass
   norm[j] = 0.f;
   const bool stop_rule = p.tol >= 0.f && p.tail[st.k] * st.C <= p.tol;
@@ -1500,7 +1505,7 @@ void ColumnEngine::pass(int force_stage) {
   int w = 8;
   while (w < last + 1) w <<= 1;
   bw_ = std::min(w, B_);
-  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_);
+  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_, -1);
   GP_LAUNCHED();
   // storage stage of this pass: FP32 until every column's warm-up has passed
   int stage = 0;
@@ -2339,7 +2344,7 @@ ColumnEngine::View ColumnEngine::view() const {
 
 void ColumnEngine::pass_device(const int* width_dev, const int* active_dev) {
   if (storage_ != GP_F32 && !pure16_) throw Error{GP_EINVAL, "device-width passes run FP32 or pure 16-bit engines"};
-  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_);
+  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_, 0);
   GP_LAUNCHED();
   SpmmArgs a;
   a.tiles = tiles_;
@@ -2369,6 +2374,11 @@ void ColumnEngine::pass_device(const int* width_dev, const int* active_dev) {
   else launch_stage<__nv_bfloat16>(a, pure16_ ? 3 : 0, st_);
   ++pass_;
   ++passes_total_;
+}
+
+void ColumnEngine::control_after() {
+  control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_, 1);
+  GP_LAUNCHED();
 }
 
 std::vector<int> ColumnEngine::warm_columns() const {

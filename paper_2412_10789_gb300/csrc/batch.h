@@ -106,9 +106,13 @@ class ColumnEngine {
   };
   View view() const;
   // One pass whose width and busy-column count are read from device memory
-  // (set by the service's kernels): the control kernel, then the fused SpMM
-  // step, which returns at once while no column is busy.
+  // (set by the service's kernels): the control kernel for the columns that
+  // have not run a pass yet, then the fused SpMM step, which returns at once
+  // while no column is busy.
   void pass_device(const int* width_dev, const int* active_dev);
+  // The stop rule and next coefficient of the columns that ran the last
+  // device-width pass, right after it (pass_device treats only new columns).
+  void control_after();
   // Smallest pass width the engine's kernels accept (a 16-bit lane owns 16 columns).
   int min_width() const { return pure16_ && B_ >= 16 ? 16 : 8; }
   // An FP32 engine whose columns will move to a 16-bit engine of `storage`:

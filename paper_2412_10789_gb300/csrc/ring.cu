@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kRingThreads) ring_complete_kernel(RingCtl* ct
   }
 }
 
-// FP32 columns past their own warm-up (newest term Q_k with k >= warm + 3, so
+// FP32 columns past their own warm-up (newest term Q_j with j >= warm + 3, so
 // every 16-bit term has index >= warm + 2) paired with free 16-bit slots; the
 // slot records move with them.  A column moves only while at least
 // kMinSteps16 steps are certain to remain (k_low - k): moving costs a copy of
@@ -283,8 +283,9 @@ __global__ void __launch_bounds__(kRingThreads) ring_migrate_select_kernel(RingD
   __shared__ int s_from[kRingThreads];
   __shared__ int s_to[kRingThreads];
   const int j = threadIdx.x;
-  const int cand = j < B32 && s32[j].busy && !st32[j].done && st32[j].k >= s32[j].warm + 3 &&
-                   s32[j].k_low - st32[j].k >= kMinSteps16;
+  // after the pass and its control, an active column's newest term is Q_{k-1}
+  const int cand = j < B32 && s32[j].busy && !st32[j].done && st32[j].k - 1 >= s32[j].warm + 3 &&
+                   s32[j].k_low - (st32[j].k - 1) >= kMinSteps16;
   int ncand = 0;
   const int rc = block_rank(cand, s_scan, &ncand);
   if (cand) s_from[rc] = j;
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kRingThreads) ring_migrate_select_kernel(RingD
   if (j < take) {
     const int a = s_from[j], b = s_to[j];
     SlotDev sd = s32[a];
-    sd.k16 = st32[a].k - 1;  // Q_k and Q_{k-1} are rounded: the first 16-bit term is Q_{k-1}
+    sd.k16 = st32[a].k - 2;  // Q_{k-1} and Q_{k-2} are rounded: the first 16-bit term is Q_{k-2}
     s16[b] = sd;
     s32[a].busy = 0;
     from[j] = a;
@@ -548,6 +549,9 @@ void RingLoop::iterate() {
     GP_LAUNCHED();
     e16_->pass_device(cnt_ + 3, &dev_->active16);
   }
+  // the stop rule on the norms of this pass, so finished columns retire now
+  e32_->control_after();
+  if (e16_) e16_->control_after();
   // retirement: outputs, done records, freed columns
   auto retire = [&](ColumnEngine& e, SlotDev* slots, int* ret, int* count, int block16) {
     const ColumnEngine::View w = e.view();
