@@ -1139,53 +1139,6 @@ __global__ void prop_isolated_kernel(int64_t n, int64_t na, const int32_t* newid
   }
 }
 
-// Columns of an FP32 engine into a 16-bit engine: per row, Q_k and Q_{k-1}
-// rounded to the 16-bit storage as the 16-bit passes store them (BF16 round to
-// nearest; FP16 of Q * 2^12), and y.  A warp per row, its lanes over the
-// columns moved.
-template <typename H>
-__device__ __forceinline__ H to_storage(float x);
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
-template <>
-__device__ __forceinline__ __half to_storage<__half>(float x) { return __float2half_rn(x * kF16Scale); }
-
-template <typename H>
-__global__ void migrate_columns_kernel(int64_t na, int ldb_s, int ldb_d, const int* src_cols, const int* dst_cols,
-                                       int nc, const float* fk, const float* fk1, const float* ys, H* hk, H* hk1,
-                                       float* yd) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
-    for (int t = lane; t < nc; t += 32) {
-      const int64_t a = r * ldb_s + src_cols[t], b = r * ldb_d + dst_cols[t];
-      hk[b] = to_storage<H>(fk[a]);
-      hk1[b] = to_storage<H>(fk1[a]);
-      yd[b] = ys[a];
-    }
-  }
-}
-
-// The per-column state of the moved columns (one block per column), and the
-// source column cleared (inactive, no stop record).
-__global__ void migrate_state_kernel(const int* src_cols, const int* dst_cols, ColState* cs_s, const ColParam* cp_s,
-                                     ColStat* st_s, float* nm_s, ColState* cs_d, ColParam* cp_d, ColStat* st_d,
-                                     float* nm_d) {
-  const int a = src_cols[blockIdx.x], b = dst_cols[blockIdx.x];
-  const float* from = reinterpret_cast<const float*>(cp_s + a);
-  float* to = reinterpret_cast<float*>(cp_d + b);
-  for (int i = threadIdx.x; i < (int)(sizeof(ColParam) / sizeof(float)); i += blockDim.x) to[i] = from[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cs_d[b] = cs_s[a];
-    st_d[b] = st_s[a];
-    nm_d[b] = nm_s[a];
-    cs_s[a] = ColState{0, 0.f};
-    st_s[a] = ColStat{0, 0, 0, 0.f};
-    nm_s[a] = 0.f;
-  }
-}
-
 int device_sms() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1262,7 +1215,7 @@ int warm_step(const std::vector<double>& c, int kcap, double warmup_tail) {
 }
 
 ColumnEngine::ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long, bool pure16)
-    : g_(g), B_(B), bw_(B), storage_(storage), warm_storage_(storage), pure16_(pure16), st_(st) {
+    : g_(g), B_(B), bw_(B), storage_(storage), pure16_(pure16), st_(st) {
   if (B < 8 || B > 256 || (B & (B - 1)))
     throw Error{GP_EINVAL, "block width must be a power of two in [8, 256]"};
   if (t_long <= 0) t_long = g.cfg.t_heavy > 0 ? g.cfg.t_heavy - 1 : kBTileCap;
@@ -1438,10 +1391,7 @@ std::vector<int> ColumnEngine::admit(const std::vector<gp_request>& reqs, std::v
     p.kstop = r.k_rule == GP_K_FIXED ? r.k_fixed
               : r.k_rule == GP_K_PAPER ? std::min(kcap - 1, paper_k(r.function, r.param, r.l1_tol))
                                        : 0;
-    p.warm = warm_step(c, kcap, column_warm_tail(g_.cfg.warmup_tail, warm_storage_, r.l1_tol));
-    slots_[slot].pass_admit = passes_total_;
-    slots_[slot].warm = p.warm;
-    slots_[slot].k16_from = -1;
+    p.warm = warm_step(c, kcap, column_warm_tail(g_.cfg.warmup_tail, storage_, r.l1_tol));
     params.push_back(p);
     cols.push_back(slot);
     srcs.push_back(g_.h_newid[r.source]);
@@ -1585,7 +1535,7 @@ std::vector<ColumnEngine::Finished> ColumnEngine::collect(bool force_all) {
     f.C = stat[j].C;
     f.tail_bound = kCMargin * (double)slots_[j].tails[std::min(f.K, kMaxColK - 1)] * stat[j].C;
     f.t_admit = slots_[j].t_admit;
-    f.k16_from = slots_[j].k16_from >= 0 ? slots_[j].k16_from : h_pass_ >= 0 ? h_pass_ : f.K + 1;
+    f.k16_from = h_pass_ >= 0 ? h_pass_ : f.K + 1;
     fin.push_back(f);
     slots_[j].busy = false;
     const ColStat zero{0, 0, 0, 0.f};
@@ -2379,63 +2329,6 @@ void ColumnEngine::pass_device(const int* width_dev, const int* active_dev) {
 void ColumnEngine::control_after() {
   control_kernel<<<(B_ + 127) / 128, 128, 0, st_>>>(col_, par_, stat_, norm_, B_, kcap_, tile_ctr_, 1);
   GP_LAUNCHED();
-}
-
-std::vector<int> ColumnEngine::warm_columns() const {
-  std::vector<int> cols;
-  if (pure16_ || warm_storage_ == GP_F32) return cols;
-  for (int j = 0; j < B_; ++j) {
-    const Slot& sl = slots_[j];
-    if (sl.busy && (int64_t)(passes_total_ - sl.pass_admit) >= (int64_t)sl.warm + 2) cols.push_back(j);
-  }
-  return cols;
-}
-
-int ColumnEngine::adopt(ColumnEngine& src, const std::vector<int>& cols) {
-  if (!pure16_ || src.pure16_ || !src.f_[0]) throw Error{GP_EINVAL, "adopt moves FP32 columns into a 16-bit engine"};
-  if (src.st_ != st_) throw Error{GP_EINVAL, "engines exchanging columns must share a stream"};
-  std::vector<int> from, to;
-  int next = 0;
-  for (int j : cols) {
-    while (next < B_ && slots_[next].busy) ++next;
-    if (next >= B_) break;
-    from.push_back(j);
-    to.push_back(next++);
-  }
-  const int nc = (int)from.size();
-  if (nc == 0) return 0;
-  int* d_from = scratch_;  // a 16-bit engine admits nothing, so its scratch is free here
-  int* d_to = scratch_ + B_;
-  GP_CUDA_TRY(cudaMemcpyAsync(d_from, from.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st_));
-  GP_CUDA_TRY(cudaMemcpyAsync(d_to, to.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st_));
-  // the next pass of src would gather f_[src.pass_ & 1] (Q_k); this engine's next
-  // pass gathers h_[pass_ & 1]
-  const float* fk = src.f_[src.pass_ & 1];
-  const float* fk1 = src.f_[(src.pass_ + 1) & 1];
-  const int grid = device_sms() * 8;
-  if (storage_ == GP_F16)
-    migrate_columns_kernel<__half><<<grid, 256, 0, st_>>>(g_.n_active, src.B_, B_, d_from, d_to, nc, fk, fk1, src.y_,
-                                                          (__half*)h_[pass_ & 1], (__half*)h_[(pass_ + 1) & 1], y_);
-  else
-    migrate_columns_kernel<__nv_bfloat16><<<grid, 256, 0, st_>>>(
-        g_.n_active, src.B_, B_, d_from, d_to, nc, fk, fk1, src.y_, (__nv_bfloat16*)h_[pass_ & 1],
-        (__nv_bfloat16*)h_[(pass_ + 1) & 1], y_);
-  GP_LAUNCHED();
-  migrate_state_kernel<<<nc, 128, 0, st_>>>(d_from, d_to, src.col_, src.par_, src.stat_, src.norm_, col_, par_, stat_,
-                                            norm_);
-  GP_LAUNCHED();
-  GP_CUDA_TRY(cudaStreamSynchronize(st_));  // the index vectors are local
-  for (int t = 0; t < nc; ++t) {
-    Slot& d = slots_[to[t]];
-    d = src.slots_[from[t]];
-    // Q_j (j = 1 + passes since admission) and Q_{j-1} were rounded: the first
-    // 16-bit term is Q_{j-1}
-    d.k16_from = (int)(src.passes_total_ - d.pass_admit);
-    src.slots_[from[t]] = Slot{};
-    --src.active_;
-    ++active_;
-  }
-  return nc;
 }
 
 void ColumnEngine::restart() {

@@ -53,8 +53,8 @@ class ColumnEngine {
   // t_long: rows with more entries become chunk tiles (at most kBTileCap;
   // 0: from cfg.t_heavy, else kBTileCap).  pure16: a 16-bit engine (storage
   // GP_BF16 or GP_F16) without the FP32 pair, whose columns come only from an
-  // FP32 engine through adopt() once their warm-up is over (the service's
-  // second block); every pass of it gathers, reads and writes 16 bits.
+  // FP32 engine once their warm-up is over (the service's second block, filled
+  // by ring.cu); every pass of it gathers, reads and writes 16 bits.
   ColumnEngine(Graph& g, int B, gp_dtype storage, cudaStream_t st, int t_long = 0, bool pure16 = false);
   int t_long() const { return t_long_; }
   ~ColumnEngine();
@@ -79,16 +79,6 @@ class ColumnEngine {
   std::vector<Finished> collect(bool force_all);
   // Forget the pass count and the 16-bit schedule (no column may be busy).
   void restart();
-  // Busy columns whose stored terms are all past their warm-up: the newest
-  // Q_j has j >= warm + 3, so rounding Q_j and Q_{j-1} to 16 bits keeps every
-  // 16-bit term at index >= warm + 2, where the schedule of gp_batch stores
-  // its first one.  Columns of a pure16 engine are never eligible.
-  std::vector<int> warm_columns() const;
-  // Move columns `cols` of the FP32 engine `src` into free slots of this
-  // pure16 engine (as many as fit; returns how many moved): Q_k and Q_{k-1}
-  // rounded to 16 bits into the buffers this engine's next pass gathers and
-  // reads, y, the column's coefficients, state and last norm, and its request.
-  int adopt(ColumnEngine& src, const std::vector<int>& cols);
   bool pure16() const { return pure16_; }
   // Device arrays of the engine, for the device-resident service (ring.cu).
   struct View {
@@ -115,9 +105,6 @@ class ColumnEngine {
   void control_after();
   // Smallest pass width the engine's kernels accept (a 16-bit lane owns 16 columns).
   int min_width() const { return pure16_ && B_ >= 16 ? 16 : 8; }
-  // An FP32 engine whose columns will move to a 16-bit engine of `storage`:
-  // their warm-up steps follow that storage's threshold (column_warm_tail).
-  void hand_over_to(gp_dtype storage) { warm_storage_ = storage; }
   // Move the busy columns into the first half of the pass width once at most
   // half of it is busy.  Returns whether the width was halved.
   bool compact();
@@ -146,9 +133,6 @@ class ColumnEngine {
     uint64_t tag = 0;
     std::chrono::steady_clock::time_point t_admit;
     std::vector<double> tails;  // FP64 tail(k) for the report
-    uint64_t pass_admit = 0;    // passes_total_ at admission: Q_j, j = 1 + passes since
-    int warm = 0;               // the column's warm-up step (warm_step)
-    int k16_from = -1;          // first term stored in 16 bits once migrated (else -1)
   };
 
   Graph& g_;
@@ -156,7 +140,6 @@ class ColumnEngine {
   int t_long_ = 0;  // rows with more entries are chunk tiles
   int bw_ = 0;  // columns of each pass (a prefix of B_)
   gp_dtype storage_;
-  gp_dtype warm_storage_;  // storage whose warm-up threshold the columns' warm step follows
   bool pure16_ = false;
   cudaStream_t st_;
   int kcap_ = 0;

@@ -454,10 +454,7 @@ RingLoop::RingLoop(Graph& g, int width, gp_dtype storage, cudaStream_t st) : g_(
   try {
     const bool two = storage == GP_BF16 || storage == GP_F16;
     e32_.reset(new ColumnEngine(g, width, GP_F32, st));
-    if (two) {
-      e32_->hand_over_to(storage);
-      e16_.reset(new ColumnEngine(g, width, storage, st, 0, true));
-    }
+    if (two) e16_.reset(new ColumnEngine(g, width, storage, st, 0, true));
     cap_req_ = 1024;
     cap_done_ = 4096;
     mapped_alloc(&ctl_, &ctl_d_, 1);
