@@ -546,3 +546,36 @@ def test_serving_request_ring_wraps(gp):
             assert np.abs(Y[i] - Y[i % len(srcs)]).sum() <= 1e-4
     finally:
         dg.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_serving_staggered_arrivals(gp, storage):
+    """Requests arriving in waves while earlier ones are mid-flight join the
+    running block (continuous batching on the device): mixed functions and
+    tolerances on a Chung-Lu graph, every result within its tolerance of the
+    oracle, and in FP32 each ticket's K within one step of the oracle's own
+    stop."""
+    g = graph("chunglu20k")
+    srcs = [int(s) for s in gg.sources(g, 60, 43)]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=32,
+                            storage=STORAGES[storage])
+    try:
+        ys = _outputs(g, len(srcs))
+        spec = []
+        tickets = []
+        for wave in range(6):
+            for i in range(wave * 10, wave * 10 + 10):
+                fn, p = MIX[i % len(MIX)]
+                tol = [1e-4, 1e-5, 1e-6][i % 3]
+                spec.append((fn, p, tol))
+                tickets.append(gp.gp_submit(dg, gp.make_request(fn, srcs[i], p, tol, ys[i])))
+            time.sleep(0.003)
+        infos = [gp.gp_wait(dg, t, 120000.0) for t in tickets]
+        for i, (fn, p, tol) in enumerate(spec):
+            ystar = O.chebypower(g, srcs[i], KINDS[fn], p, 150)
+            assert O.errors(g, ystar, ys[i].cpu().numpy())["l1"] <= tol, (i, infos[i])
+            if storage == "f32":  # 16-bit terms move the measured norms, and with them K
+                _, Ko, _ = O.chebypower_tol(g, srcs[i], KINDS[fn], p, tol)
+                assert abs(infos[i]["K"] - Ko) <= 1, (i, infos[i], Ko)
+    finally:
+        dg.close()
