@@ -74,8 +74,8 @@ def parse():
                    help="rmat22: the headline single-source workload; the others time the batched and "
                         "served forms on the larger graphs")
     p.add_argument("--requests", type=int, default=10000, help="chunglu24_serve: requests per load level")
-    p.add_argument("--serve-width", type=int, default=256,
-                   help="query slots of the service block (a power of two, <= 512)")
+    p.add_argument("--serve-width", type=int, default=0,
+                   help="query slots of the service block (a power of two, <= 512; 0: the autotuned width)")
     p.add_argument("--loads", default="0.5,0.8,0.95", help="chunglu24_serve: offered load levels")
     p.add_argument("--serve-storage", default="fp32", choices=["fp32", "bf16", "fp16"],
                    help="chunglu24_serve: storage of the service's blocks")
@@ -242,13 +242,15 @@ def bench_serving(gp, g, queries, dev, world, nreq=1024, loads=(0.5, 0.8, 0.95),
     16-bit block after its own warm-up."""
     import torch
     st = {"fp32": gp.GP_F32, "bf16": gp.GP_BF16, "fp16": gp.GP_F16}[storage]
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=width, storage=st)
+    # width 0: the service takes the autotuner's width for this graph
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=width, storage=st,
+                            autotune=1 if width == 0 else 0)
     specs = [queries[i % len(queries)] + (tols[i % len(tols)],) for i in range(nreq)]
-    pool = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range(width + 64)]
+    pool = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range((width or 256) + 64)]
     dist_barrier(world)
     res, kept = serve_levels(gp, dg, specs, pool, loads, 7, keep=sample)
     dg.close()
-    res.update({"storage": storage, "block_width": width,
+    res.update({"storage": storage, "block_width": width or "autotuned",
                 "workload": "the step's queries, tolerances " + "/".join(f"{t:g}" for t in tols),
                 "arrivals": "saturated: all at once; load_x: Poisson at x times the saturated rate"})
     outs = {name: {"tol": {i: specs[i][3] for i in sample}, "y": {i: _host(kept[i]) for i in sample}}}
@@ -727,8 +729,9 @@ def serve_poisson(gp, g, dev, args):
     tols = rng.choice([1e-4, 1e-5, 1e-6], nreq)
     specs = [(int(f), int(s), float(p), float(t)) for f, s, p, t in zip(fns, srcs, params, tols)]
     st = {"fp32": gp.GP_F32, "bf16": gp.GP_BF16, "fp16": gp.GP_F16}[args.serve_storage]
-    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=args.serve_width, storage=st)
-    pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range(args.serve_width + 64)]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=args.serve_width, storage=st,
+                            autotune=1 if args.serve_width == 0 else 0)
+    pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range((args.serve_width or 256) + 64)]
     sample = list(range(min(args.cpu_sample, nreq)))
     res, kept = serve_levels(gp, dg, specs, pool, [float(x) for x in args.loads.split(",")], 5, keep=sample)
     res["storage"] = args.serve_storage

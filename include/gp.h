@@ -285,7 +285,8 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
  * one step per fused SpMM pass, retires a column when its stop rule fires
  * (writing y_out before the ticket completes) and refills the slot.  The
  * block has as many slots as the memory budget allows (cfg.mem_budget, default
- * 80% of the free device memory), at most cfg.block_width (0: 256; 512 at most),
+ * 80% of the free device memory), at most cfg.block_width (0: with cfg.autotune
+ * the width gp_autotune picks for FP32 on this graph, else 256; 512 at most),
  * a power of two; a block wider than 256 columns runs as 256-column halves,
  * each with its own pass.  With cfg.storage GP_BF16 or GP_F16 a second block of
  * the same width stores 16 bits: every request starts in the FP32 block and

@@ -449,12 +449,13 @@ void mapped_alloc(T** host, T** dev, size_t count) {
 
 }  // namespace
 
-RingLoop::RingLoop(Graph& g, int width, gp_dtype storage, cudaStream_t st) : g_(g), B_(width), st_(st) {
+RingLoop::RingLoop(Graph& g, int width, gp_dtype storage, cudaStream_t st, int t_long)
+    : g_(g), B_(width), st_(st) {
   if (width < 8 || width > kRingThreads) throw Error{GP_EINVAL, "a ring block has 8 to 256 columns"};
   try {
     const bool two = storage == GP_BF16 || storage == GP_F16;
-    e32_.reset(new ColumnEngine(g, width, GP_F32, st));
-    if (two) e16_.reset(new ColumnEngine(g, width, storage, st, 0, true));
+    e32_.reset(new ColumnEngine(g, width, GP_F32, st, t_long));
+    if (two) e16_.reset(new ColumnEngine(g, width, storage, st, t_long, true));
     cap_req_ = 1024;
     cap_done_ = 4096;
     mapped_alloc(&ctl_, &ctl_d_, 1);

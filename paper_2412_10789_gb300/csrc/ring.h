@@ -71,7 +71,8 @@ namespace gp {
 // 16-bit block of the same width, driven by the device-resident loop.
 class RingLoop {
  public:
-  RingLoop(Graph& g, int width, gp_dtype storage, cudaStream_t st);
+  // t_long: rows with more entries are chunked (0: the engines' default).
+  RingLoop(Graph& g, int width, gp_dtype storage, cudaStream_t st, int t_long = 0);
   ~RingLoop();
   RingLoop(const RingLoop&) = delete;
   RingLoop& operator=(const RingLoop&) = delete;

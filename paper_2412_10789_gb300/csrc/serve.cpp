@@ -14,7 +14,8 @@
 //
 // The block has as many columns as the memory budget allows (cfg.mem_budget,
 // default 80% of the free device memory, at ColumnEngine::bytes_per_column
-// each), capped by cfg.block_width (256 by default, 512 at most); a block of
+// each), capped by cfg.block_width (with cfg.autotune and no width, the
+// autotuned width; else 256; 512 at most); a block of
 // more than 256 columns runs as 256-column halves, each its own loop.  With
 // 16-bit storage (cfg.storage GP_BF16 or GP_F16) each half has an FP32 block
 // for admission and a 16-bit block of the same width: a column moves to the
@@ -258,9 +259,19 @@ Serve* get_serve(Graph& g) {
   s->storage = two_blocks ? storage : GP_F32;
   const size_t per_col = ColumnEngine::bytes_per_column(g, GP_F32) +
                          (two_blocks ? ColumnEngine::bytes_per_column(g, storage, true) : 0);
-  // 256 slots already keep the GPU busy on large graphs; more slots add
-  // concurrency, not throughput, and lengthen every pass (latency under load)
-  const int cap = std::min(g.cfg.block_width > 0 ? g.cfg.block_width : kServeDefaultWidth, kServeMaxWidth);
+  // The width: cfg.block_width, else with cfg.autotune the autotuner's width
+  // for this graph (the width of least device time per column and pass; a
+  // narrower block also shortens every pass, so latency under load drops
+  // too), else 256 (more slots add concurrency, not throughput).
+  int cap = kServeDefaultWidth, t_long = 0;
+  if (g.cfg.block_width > 0) {
+    cap = g.cfg.block_width;
+  } else if (g.cfg.autotune) {
+    const TunedBlock tb = tune_block(g, GP_F32, {});
+    cap = tb.B;
+    t_long = tb.t_long;
+  }
+  cap = std::min(cap, kServeMaxWidth);
   int width = 8;
   while (width * 2 <= cap && (size_t)(width * 2) * per_col <= budget) width *= 2;
   if ((size_t)width * per_col > budget) throw Error{GP_ENOMEM, "memory budget is below eight query columns"};
@@ -269,7 +280,7 @@ Serve* get_serve(Graph& g) {
   s->events.resize(kAhead, nullptr);
   for (auto& e : s->events) GP_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (int c0 = 0; c0 < width; c0 += kEngineMaxWidth)
-    s->loops.emplace_back(new RingLoop(g, std::min(width - c0, kEngineMaxWidth), storage, s->stream));
+    s->loops.emplace_back(new RingLoop(g, std::min(width - c0, kEngineMaxWidth), storage, s->stream, t_long));
   for (int i = kStaging - 1; i >= 0; --i) s->staging_free.push_back(i);
   s->th = std::thread([p = s.get()] { p->run(); });
   g.serve = s.release();
