@@ -53,7 +53,7 @@ typedef enum {
   GP_ENOTFOUND = 5,  /* gp_poll: unknown ticket */
   GP_ETIMEDOUT = 6,  /* gp_wait: the ticket did not complete within the timeout */
   GP_EBUSY = 7,      /* the serving queue is full */
-  GP_ENOTSUP = 8     /* a combination of options this build does not support */
+  GP_ENOTSUP = 8     /* a combination of options the library does not support */
 } gp_status;
 
 typedef enum { GP_F32 = 0, GP_F64 = 1, GP_BF16 = 2, GP_F16 = 3 } gp_dtype;

@@ -1,5 +1,5 @@
 // C ABI entry points: argument checks, the exception-to-status guard, the
-// thread-local error message, and dispatch to the drivers.
+// thread-local error message, and dispatch to the query functions.
 #include <cstring>
 #include <exception>
 #include <functional>
