@@ -7,11 +7,16 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gp_internal.h"
 
 namespace gp {
 
 std::atomic<uint64_t> g_launches{0};
+
+TraceRange::TraceRange(const char* name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
 
 namespace {
 thread_local std::string t_last_error;
@@ -82,6 +87,7 @@ extern "C" void gp_config_default(gp_config* cfg) {
 
 extern "C" gp_status gp_ppr(gp_graph* gh, int32_t source, double alpha, double l1_tol, gp_dtype out_dtype,
                             void* y_out, int y_on_device, gp_query_info* info) {
+  TraceRange trace("gp_ppr");
   return guard([&] {
     Graph* g = as_graph(gh);
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -92,6 +98,7 @@ extern "C" gp_status gp_ppr(gp_graph* gh, int32_t source, double alpha, double l
 
 extern "C" gp_status gp_hkpr(gp_graph* gh, int32_t source, double t, double l1_tol, gp_dtype out_dtype,
                              void* y_out, int y_on_device, gp_query_info* info) {
+  TraceRange trace("gp_hkpr");
   return guard([&] {
     Graph* g = as_graph(gh);
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -101,6 +108,7 @@ extern "C" gp_status gp_hkpr(gp_graph* gh, int32_t source, double t, double l1_t
 }
 
 extern "C" gp_status gp_query(gp_graph* gh, const gp_request* req, gp_query_info* info) {
+  TraceRange trace("gp_query");
   return guard([&] {
     Graph* g = as_graph(gh);
     GP_REQUIRE(req, "request is NULL");
@@ -111,6 +119,7 @@ extern "C" gp_status gp_query(gp_graph* gh, const gp_request* req, gp_query_info
 
 extern "C" gp_status gp_power(gp_graph* gh, int32_t function, int32_t source, double param, double l1_tol,
                               gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info) {
+  TraceRange trace("gp_power");
   return guard([&] {
     Graph* g = as_graph(gh);
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -120,6 +129,7 @@ extern "C" gp_status gp_power(gp_graph* gh, int32_t function, int32_t source, do
 }
 
 extern "C" gp_status gp_batch(gp_graph* gh, int32_t count, const gp_request* reqs, gp_query_info* infos) {
+  TraceRange trace("gp_batch");
   return guard([&] {
     Graph* g = as_graph(gh);
     GP_REQUIRE(count >= 0, "count must be >= 0");
@@ -157,6 +167,7 @@ extern "C" gp_status gp_wait(gp_graph* gh, uint64_t ticket, double timeout_ms, g
 }
 
 extern "C" gp_status gp_batch_clenshaw(gp_graph* gh, int32_t count, const gp_request* reqs, gp_query_info* infos) {
+  TraceRange trace("gp_batch_clenshaw");
   return guard([&] {
     Graph* g = as_graph(gh);
     GP_REQUIRE(count >= 0, "count must be >= 0");
@@ -168,6 +179,7 @@ extern "C" gp_status gp_batch_clenshaw(gp_graph* gh, int32_t count, const gp_req
 
 extern "C" gp_status gp_propagate(gp_graph* gh, int32_t function, double param, double a, int32_t F, const float* X,
                                    float* Z, int on_device, double l1_tol, gp_query_info* infos) {
+  TraceRange trace("gp_propagate");
   return guard([&] {
     Graph* g = as_graph(gh);
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -177,6 +189,7 @@ extern "C" gp_status gp_propagate(gp_graph* gh, int32_t function, double param, 
 
 extern "C" gp_status gp_chebypush(gp_graph* gh, int32_t function, int32_t source, double param, double eps_a,
                                    int32_t K, gp_dtype out_dtype, void* y_out, int y_on_device, gp_query_info* info) {
+  TraceRange trace("gp_chebypush");
   return guard([&] {
     Graph* g = as_graph(gh);
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -187,6 +200,7 @@ extern "C" gp_status gp_chebypush(gp_graph* gh, int32_t function, int32_t source
 extern "C" gp_status gp_ppr_bidirectional(gp_graph* gh, int32_t source, double alpha, double eps_r, double delta,
                                            int32_t K, uint64_t seed, gp_dtype out_dtype, void* y_out,
                                            int y_on_device, gp_query_info* info) {
+  TraceRange trace("gp_ppr_bidirectional");
   return guard([&] {
     Graph* g = as_graph(gh);
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -196,6 +210,7 @@ extern "C" gp_status gp_ppr_bidirectional(gp_graph* gh, int32_t source, double a
 
 extern "C" gp_status gp_autotune(gp_graph* gh, gp_dtype storage, const int32_t* widths, int32_t nwidths,
                                   int32_t* best_width, int32_t* best_t_heavy, double* us_per_column_pass) {
+  TraceRange trace("gp_autotune");
   return guard([&] {
     Graph* g = as_graph(gh);
     GP_REQUIRE(best_width, "best_width is NULL");

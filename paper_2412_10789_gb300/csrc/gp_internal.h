@@ -37,6 +37,15 @@ gp_status guard(const std::function<void()>& f);
     if (!(cond)) throw ::gp::Error{GP_EINVAL, std::string(msg)}; \
   } while (0)
 
+// A named NVTX range for the lifetime of the object (the calls of the C ABI and
+// the service's iterations), so that Nsight timelines group their kernels.
+struct TraceRange {
+  explicit TraceRange(const char* name);
+  ~TraceRange();
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
 extern std::atomic<uint64_t> g_launches;
 inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 

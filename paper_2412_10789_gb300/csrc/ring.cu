@@ -522,6 +522,7 @@ void RingLoop::take_done(std::vector<RingDone>& out) {
 int RingLoop::active() const { return __atomic_load_n(&ctl_->active, __ATOMIC_RELAXED); }
 
 void RingLoop::iterate() {
+  TraceRange trace("gp_serve_iteration");
   const int sms = ring_sms();
   const int64_t na = g_.n_active;
   ColumnEngine::View v = e32_->view();
