@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--forms", default="single,batched,serving",
                    help="comma list of the forms to time (without 'single' only the named forms run, for "
                         "profiling; the line's value is then null)")
-    p.add_argument("--serve-legs", default="serving,serving_bf16,serving_bf16_tol1e-4",
+    p.add_argument("--serve-legs", default="serving,serving_bf16,serving_bf16_tol1e-4,serving_fp16_tol1e-4",
                    help="served forms of the rmat22 workload to time")
     p.add_argument("--serve-requests", type=int, default=1024,
                    help="rmat22 serving leg: requests per arrival pattern")
@@ -246,7 +246,10 @@ def bench_serving(gp, g, queries, dev, world, nreq=1024, loads=(0.5, 0.8, 0.95),
     dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=width, storage=st,
                             autotune=1 if width == 0 else 0)
     specs = [queries[i % len(queries)] + (tols[i % len(tols)],) for i in range(nreq)]
-    pool = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range((width or 256) + 64)]
+    # enough output buffers to keep every slot busy: a 16-bit service has a
+    # second block of the same width
+    blocks = 1 if storage == "fp32" else 2
+    pool = [torch.empty(g.n, dtype=torch.float64, device=dev) for _ in range(blocks * (width or 256) + 64)]
     dist_barrier(world)
     res, kept = serve_levels(gp, dg, specs, pool, loads, 7, keep=sample)
     dg.close()
@@ -632,6 +635,7 @@ def run_ours(args, rank, world):
         legs = set(args.serve_legs.split(","))
         for name, storage, tols in (("serving", "fp32", (1e-4, 1e-5, 1e-6)),
                                     ("serving_bf16", "bf16", (1e-4, 1e-5, 1e-6)),
+                                    ("serving_fp16", "fp16", (1e-4, 1e-5, 1e-6)),
                                     ("serving_fp32_tol1e-4", "fp32", (1e-4,)),
                                     ("serving_bf16_tol1e-4", "bf16", (1e-4,)),
                                     ("serving_fp16_tol1e-4", "fp16", (1e-4,))):
@@ -641,10 +645,10 @@ def run_ours(args, rank, world):
                                                 storage=storage, tols=tols, name=name, width=args.serve_width)
             captured.update(outs)
         single4 = (batched or {}).get("bf16_tol1e-4", {}).get("single_source_same_tol")
-        if single4 and "serving_bf16_tol1e-4" in serving:
-            serving["serving_bf16_tol1e-4"]["single_source_same_tol"] = single4
-            serving["serving_bf16_tol1e-4"]["vs_single_source_same_tol"] = \
-                serving["serving_bf16_tol1e-4"]["saturated"]["value"] / single4
+        for name in ("serving_fp32_tol1e-4", "serving_bf16_tol1e-4", "serving_fp16_tol1e-4"):
+            if single4 and name in serving:
+                serving[name]["single_source_same_tol"] = single4
+                serving[name]["vs_single_source_same_tol"] = serving[name]["saturated"]["value"] / single4
     # ---- CPU oracle baseline and the errors of every result (rank 0, N = 1 only)
     cpu = errors = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -731,7 +735,9 @@ def serve_poisson(gp, g, dev, args):
     st = {"fp32": gp.GP_F32, "bf16": gp.GP_BF16, "fp16": gp.GP_F16}[args.serve_storage]
     dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=args.serve_width, storage=st,
                             autotune=1 if args.serve_width == 0 else 0)
-    pool = [torch.empty(g.n, dtype=torch.float32, device=dev) for _ in range((args.serve_width or 256) + 64)]
+    blocks = 1 if args.serve_storage == "fp32" else 2
+    pool = [torch.empty(g.n, dtype=torch.float32, device=dev)
+            for _ in range(blocks * (args.serve_width or 256) + 64)]
     sample = list(range(min(args.cpu_sample, nreq)))
     res, kept = serve_levels(gp, dg, specs, pool, [float(x) for x in args.loads.split(",")], 5, keep=sample)
     res["storage"] = args.serve_storage

@@ -291,8 +291,11 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
  * each with its own pass.  With cfg.storage GP_BF16 or GP_F16 a second block of
  * the same width stores 16 bits: every request starts in the FP32 block and
  * moves to the 16-bit block once its own warm-up is over (see warmup_tail)
- * if at least six more steps are certain to follow (info.k16_from reports the
- * first term stored in 16 bits, K + 1 if none); with GP_F32 the service stores
+ * and at least one more step is certain to follow, while the FP32 block is
+ * busy (its columns and the waiting requests fill more than half of it) and
+ * the 16-bit block would then hold at least min(64, width / 4) columns
+ * (info.k16_from reports the first term stored in 16 bits, K + 1 if none);
+ * under light load a request stays in FP32.  With GP_F32 the service stores
  * FP32 only.  Admission, retirement, outputs and slot refills are decided on
  * the device every pass (a request loop in mapped host memory), and a lightly
  * loaded block packs its columns so that its passes narrow.  The request's y_out must stay valid

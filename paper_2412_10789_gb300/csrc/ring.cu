@@ -120,21 +120,38 @@ __global__ void __launch_bounds__(kRingThreads) ring_admit_kernel(RingCtl* ctl, 
   }
 }
 
-// Zero the new columns of Q_a, Q_b and y over all rows (a warp per row).
+// Calls f(r, t) for every row r < na and item t < nc (a column being reset,
+// moved or migrated).  With more than 16 items a warp takes one row at a time,
+// its lanes over the items; with fewer, P >= nc lanes take a row and a warp
+// covers 32 / P rows at a time, so that more rows' accesses are in flight.
+template <typename F>
+__device__ __forceinline__ void for_rows_items(int64_t na, int nc, F f) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (nc <= 16) {
+    int P = 1;
+    while (P < nc) P <<= 1;
+    const int rows = 32 / P, t = lane & (P - 1);
+    if (t >= nc) return;
+    for (int64_t r = w0 * rows + lane / P; r < na; r += nw * rows) f(r, t);
+    return;
+  }
+  for (int64_t r = w0; r < na; r += nw)
+    for (int t = lane; t < nc; t += 32) f(r, t);
+}
+
+// Zero the new columns of Q_a, Q_b and y over all rows.
 __global__ void ring_reset_kernel(int64_t na, int B, const int* new_list, const RingDev* dev, float* fa, float* fb,
                                   float* y) {
   const int nc = dev->new_count;
   if (nc == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
-    for (int t = lane; t < nc; t += 32) {
-      const int64_t i = r * B + new_list[t];
-      fa[i] = 0.f;
-      fb[i] = 0.f;
-      y[i] = 0.f;
-    }
-  }
+  for_rows_items(na, nc, [&](int64_t r, int t) {
+    const int64_t i = r * B + new_list[t];
+    fa[i] = 0.f;
+    fb[i] = 0.f;
+    y[i] = 0.f;
+  });
 }
 
 // r_0 = e_s (Q_0 = e_s / d_s), r_1 = P e_s (Q_1(v) = 1 / (d_s d_v) for v in
@@ -273,23 +290,47 @@ __global__ void __launch_bounds__(kRingThreads) ring_complete_kernel(RingCtl* ct
 // FP32 columns past their own warm-up (newest term Q_j with j >= warm + 3, so
 // every 16-bit term has index >= warm + 2) paired with free 16-bit slots; the
 // slot records move with them.  A column moves only while at least
-// kMinSteps16 steps are certain to remain (k_low - k): moving costs a copy of
-// its rows, which a few cheaper 16-bit steps do not repay.
-constexpr int kMinSteps16 = 6;
-__global__ void __launch_bounds__(kRingThreads) ring_migrate_select_kernel(RingDev* dev, SlotDev* s32,
-                                                                           const ColStat* st32, int B32, SlotDev* s16,
-                                                                           int B16, int* from, int* to) {
+// kMinSteps16 steps are certain to remain (k_low - k), only while the FP32
+// block is busy (its busy columns and the requests waiting in the ring fill
+// more than half of its slots), and only when the 16-bit block would then hold
+// at least kMinCols16 columns (a quarter of its slots at most).  A move frees
+// an FP32 slot for the next request and the column's later steps run in 16
+// bits.  But every iteration with a column in each block runs two passes, and
+// a 16-bit pass over a few columns costs nearly as much as one over many (its
+// time is set by the latency of gathering every col_idx entry: at 16 columns
+// it costs more per column than a full FP32 pass), so under light load, or
+// with too few columns past their warm-up, columns stay in FP32 and each
+// iteration stays one pass long.
+#ifndef GP_MIN_STEPS16
+#define GP_MIN_STEPS16 1
+#endif
+#ifndef GP_MIN_COLS16
+#define GP_MIN_COLS16 64
+#endif
+constexpr int kMinSteps16 = GP_MIN_STEPS16;
+constexpr int kMinCols16 = GP_MIN_COLS16;
+__global__ void __launch_bounds__(kRingThreads) ring_migrate_select_kernel(const RingCtl* ctl, RingDev* dev,
+                                                                           SlotDev* s32, const ColStat* st32, int B32,
+                                                                           SlotDev* s16, int B16, int* from, int* to) {
   __shared__ int s_scan[kRingThreads];
   __shared__ int s_from[kRingThreads];
   __shared__ int s_to[kRingThreads];
+  __shared__ int s_busy;
   const int j = threadIdx.x;
+  if (j == 0) {
+    const uint64_t waiting = load_acquire_sys(&ctl->tail) - dev->head;
+    s_busy = 2 * (waiting + (uint64_t)dev->active32) > (uint64_t)B32;
+  }
+  __syncthreads();
   // after the pass and its control, an active column's newest term is Q_{k-1}
-  const int cand = j < B32 && s32[j].busy && !st32[j].done && st32[j].k - 1 >= s32[j].warm + 3 &&
+  const int cand = s_busy && j < B32 && s32[j].busy && !st32[j].done && st32[j].k - 1 >= s32[j].warm + 3 &&
                    s32[j].k_low - (st32[j].k - 1) >= kMinSteps16;
   int ncand = 0;
   const int rc = block_rank(cand, s_scan, &ncand);
   if (cand) s_from[rc] = j;
-  const int fr = j < B16 && !s16[j].busy;
+  const int need = kMinCols16 < B16 / 4 ? kMinCols16 : B16 / 4;
+  const int go = ncand > 0 && need > 0 && ncand + dev->active16 >= need;
+  const int fr = go && j < B16 && !s16[j].busy;
   int nfree = 0;
   const int rf = block_rank(fr, s_scan, &nfree);
   if (fr) s_to[rf] = j;
@@ -319,23 +360,20 @@ template <>
 __device__ __forceinline__ __half ring_to16<__half>(float x) { return __float2half_rn(x * 4096.0f); }
 
 // Q_k, Q_{k-1} (rounded as the 16-bit passes store them: BF16 round to nearest,
-// FP16 of Q * 2^12) and y of the selected columns, a warp per row.
+// FP16 of Q * 2^12) and y of the selected columns, rows spread over the warps
+// by for_rows_items.
 template <typename H>
 __global__ void ring_migrate_columns_kernel(int64_t na, int ldb_s, int ldb_d, const int* from, const int* to,
                                             const RingDev* dev, const float* fk, const float* fk1, const float* ys,
                                             H* hk, H* hk1, float* yd) {
   const int nc = dev->mig_count;
   if (nc == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
-    for (int t = lane; t < nc; t += 32) {
-      const int64_t a = r * ldb_s + from[t], b = r * ldb_d + to[t];
-      hk[b] = ring_to16<H>(fk[a]);
-      hk1[b] = ring_to16<H>(fk1[a]);
-      yd[b] = ys[a];
-    }
-  }
+  for_rows_items(na, nc, [&](int64_t r, int t) {
+    const int64_t a = r * ldb_s + from[t], b = r * ldb_d + to[t];
+    hk[b] = ring_to16<H>(fk[a]);
+    hk1[b] = ring_to16<H>(fk1[a]);
+    yd[b] = ys[a];
+  });
 }
 
 // The moved columns' coefficients, state and last norm (a block per column);
@@ -360,19 +398,22 @@ __global__ void ring_migrate_state_kernel(const int* from, const int* to, const 
 }
 
 // Pack a block's busy columns below the smallest power of two (at least
-// min_w) that holds them all, once no request waits in the ring, so that the
-// passes of a lightly loaded block narrow again (the width follows the highest
-// busy slot).  Columns above that width move into free slots below it; their
+// min_w) that holds them all, so that the passes of a lightly loaded block
+// narrow again (the width follows the highest busy slot): the FP32 block once
+// no request waits in the ring (admission refills its free slots first), the
+// 16-bit block in every iteration (only moves from the FP32 block fill it, and
+// its columns retire at scattered slots).  Columns above that width move into free slots below it; their
 // slot records move here, their data and state by the two kernels below.
 __global__ void __launch_bounds__(kRingThreads) ring_compact_select_kernel(const RingCtl* ctl, const RingDev* dev,
                                                                            SlotDev* slots, int B, int min_w,
-                                                                           int* from, int* to, int* count) {
+                                                                           int always, int* from, int* to,
+                                                                           int* count) {
   __shared__ int s_scan[kRingThreads];
   __shared__ int s_from[kRingThreads];
   __shared__ int s_to[kRingThreads];
   __shared__ int s_quiet;
   const int j = threadIdx.x;
-  if (j == 0) s_quiet = load_acquire_sys(&ctl->tail) == dev->head;
+  if (j == 0) s_quiet = always || load_acquire_sys(&ctl->tail) == dev->head;
   const int busy = j < B && slots[j].busy;
   int nb = 0;
   (void)block_rank(busy, s_scan, &nb);
@@ -400,22 +441,18 @@ __global__ void __launch_bounds__(kRingThreads) ring_compact_select_kernel(const
 }
 
 // Column `from[t]` of every row copied to column `to[t]` of the same block
-// (the stored pair and y), a warp per row.
+// (the stored pair and y), rows spread over the warps by for_rows_items.
 template <typename T>
 __global__ void ring_move_columns_kernel(int64_t na, int B, const int* from, const int* to, const int* count, T* a0,
                                          T* a1, float* y) {
   const int nc = *count;
   if (nc == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < na; r += nw) {
-    for (int t = lane; t < nc; t += 32) {
-      const int64_t a = r * B + from[t], b = r * B + to[t];
-      a0[b] = a0[a];
-      a1[b] = a1[a];
-      y[b] = y[a];
-    }
-  }
+  for_rows_items(na, nc, [&](int64_t r, int t) {
+    const int64_t a = r * B + from[t], b = r * B + to[t];
+    a0[b] = a0[a];
+    a1[b] = a1[a];
+    y[b] = y[a];
+  });
 }
 
 // Busy columns of both blocks after the iteration, for the host's statistics.
@@ -570,7 +607,7 @@ void RingLoop::iterate() {
   // block's next pass gathers and reads)
   if (e16_) {
     const ColumnEngine::View a = e32_->view(), b = e16_->view();
-    ring_migrate_select_kernel<<<1, kRingThreads, 0, st_>>>(dev_, slots32_, a.stat, B_, slots16_, B_, mig_from_,
+    ring_migrate_select_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, dev_, slots32_, a.stat, B_, slots16_, B_, mig_from_,
                                                             mig_to_);
     GP_LAUNCHED();
     const float* fk = a.f[a.pass & 1];
@@ -591,8 +628,8 @@ void RingLoop::iterate() {
   // a lightly loaded block packs its columns so that its passes narrow
   auto compact = [&](ColumnEngine& e, SlotDev* slots) {
     const ColumnEngine::View w = e.view();
-    ring_compact_select_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, dev_, slots, B_, e.min_width(), mig_from_,
-                                                            mig_to_, cnt_ + 4);
+    ring_compact_select_kernel<<<1, kRingThreads, 0, st_>>>(ctl_d_, dev_, slots, B_, e.min_width(),
+                                                            w.pure16 ? 1 : 0, mig_from_, mig_to_, cnt_ + 4);
     GP_LAUNCHED();
     if (w.pure16)
       ring_move_columns_kernel<uint16_t><<<sms * 8, 256, 0, st_>>>(na, B_, mig_from_, mig_to_, cnt_ + 4,
