@@ -267,6 +267,32 @@ def test_serving_matches_oracle_and_alone(gp, storage):
         dg.close()
 
 
+def test_serving_16bit_moves_only_under_load(gp):
+    """The 16-bit block of a service is used only while the FP32 block is
+    busy: requests served one at a time stay in FP32 (k16_from = K + 1, one
+    pass per iteration), and a burst of l1 1e-4 requests four times larger
+    than the block moves columns past their warm-up into the FP16 block.
+    Every result lies within its tolerance of the oracle."""
+    g = graph("rmat14")
+    srcs = [int(s) for s in gg.sources(g, 72, 29)]
+    dg = gp.gp_graph_create(g.n, g.row_ptr32(), g.col_idx, g.degree, block_width=16, storage=STORAGES["f16"])
+    try:
+        spec = [(MIX[i % len(MIX)][0], srcs[i], MIX[i % len(MIX)][1]) for i in range(72)]
+        ys = _outputs(g, 72)
+        alone = [_serve_all(gp, dg, [gp.make_request(fn, s, p, 1e-4, ys[i])])[0]
+                 for i, (fn, s, p) in enumerate(spec[:8])]
+        assert all(inf["k16_from"] == inf["K"] + 1 for inf in alone), [(inf["K"], inf["k16_from"]) for inf in alone]
+        burst = _serve_all(gp, dg, [gp.make_request(fn, s, p, 1e-4, ys[8 + i]) for i, (fn, s, p) in
+                                    enumerate(spec[8:])])
+        moved = sum(1 for inf in burst if inf["k16_from"] <= inf["K"])
+        assert moved >= len(burst) // 8, [(inf["K"], inf["k16_from"]) for inf in burst]
+        for i, (fn, s, p) in enumerate(spec):
+            ystar = O.chebypower(g, s, KINDS[fn], p, 150)
+            assert O.errors(g, ystar, ys[i].cpu().numpy())["l1"] <= 1e-4, (i, (alone + burst)[i])
+    finally:
+        dg.close()
+
+
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_serving_512_slots(gp, storage):
     """A 512-slot block (two 256-column engines; with BF16 storage two more
