@@ -297,8 +297,9 @@ gp_status gp_autotune(gp_graph* g, gp_dtype storage, const int32_t* widths, int3
  * (info.k16_from reports the first term stored in 16 bits, K + 1 if none);
  * under light load a request stays in FP32.  With GP_F32 the service stores
  * FP32 only.  Admission, retirement, outputs and slot refills are decided on
- * the device every pass (a request loop in mapped host memory), and a lightly
- * loaded block packs its columns so that its passes narrow.  The request's y_out must stay valid
+ * the device every pass (a request loop in mapped host memory; each
+ * iteration's launches are replayed as one CUDA graph), and a lightly loaded
+ * block packs its columns so that its passes narrow.  The request's y_out must stay valid
  * until gp_poll reports completion.
  * gp_poll returns GP_OK (and fills info) once the ticket is done, GP_EAGAIN
  * before that, GP_ENOTFOUND for an unknown or already-collected ticket.

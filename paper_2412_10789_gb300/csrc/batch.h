@@ -103,6 +103,12 @@ class ColumnEngine {
   // The stop rule and next coefficient of the columns that ran the last
   // device-width pass, right after it (pass_device treats only new columns).
   void control_after();
+  // Advance (or, with -1, take back) the pass count without launching: a
+  // pass_device whose launches a replayed CUDA graph makes.
+  void count_pass(int delta = 1) {
+    pass_ += delta;
+    passes_total_ += delta;
+  }
   // Smallest pass width the engine's kernels accept (a 16-bit lane owns 16 columns).
   int min_width() const { return pure16_ && B_ >= 16 ? 16 : 8; }
   // Move the busy columns into the first half of the pass width once at most

@@ -526,6 +526,10 @@ RingLoop::~RingLoop() { release(); }
 
 void RingLoop::release() {
   if (st_) cudaStreamSynchronize(st_);
+  for (cudaGraphExec_t& e : graph_) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
   e16_.reset();
   e32_.reset();
   if (ctl_) cudaFreeHost(ctl_);
@@ -560,6 +564,56 @@ int RingLoop::active() const { return __atomic_load_n(&ctl_->active, __ATOMIC_RE
 
 void RingLoop::iterate() {
   TraceRange trace("gp_serve_iteration");
+  const int par = e32_->view().pass & 1;
+  if (graph_[par]) {
+    GP_CUDA_TRY(cudaGraphLaunch(graph_[par], st_));
+    count_launch(graph_launches_[par]);
+    e32_->count_pass();
+    if (e16_) e16_->count_pass();
+    ++iters_;
+    return;
+  }
+  // the first iterations launch directly: they set up the kernels' attributes
+  // (lazily, once) outside any capture
+  if (iters_ < 2 || graphs_off_) {
+    enqueue();
+    ++iters_;
+    return;
+  }
+  const uint64_t n0 = g_launches.load();
+  cudaGraph_t graph = nullptr;
+  GP_CUDA_TRY(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+  try {
+    enqueue();
+  } catch (...) {
+    cudaStreamEndCapture(st_, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  const uint64_t n = g_launches.load() - n0;
+  GP_CUDA_TRY(cudaStreamEndCapture(st_, &graph));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    // nothing of the captured iteration ran: undo its pass counts and launch
+    // it directly, now and from here on
+    (void)cudaGetLastError();
+    e32_->count_pass(-1);
+    if (e16_) e16_->count_pass(-1);
+    g_launches.fetch_sub(n);
+    graphs_off_ = true;
+    enqueue();
+    ++iters_;
+    return;
+  }
+  graph_[par] = exec;
+  graph_launches_[par] = n;
+  GP_CUDA_TRY(cudaGraphLaunch(exec, st_));
+  ++iters_;
+}
+
+void RingLoop::enqueue() {
   const int sms = ring_sms();
   const int64_t na = g_.n_active;
   ColumnEngine::View v = e32_->view();

@@ -83,7 +83,10 @@ class RingLoop {
   int room() const;
   // Publish one request (room() must be positive).
   void publish(const RingReq& r);
-  // Launch one iteration of the loop (no wait for the device).
+  // Launch one iteration of the loop (no wait for the device).  After two
+  // direct iterations, the launches of an iteration are captured once per
+  // pass parity (the only thing that differs between iterations is which of
+  // each block's two Q buffers a pass gathers) and replayed as a CUDA graph.
   void iterate();
   // Done records the device has made visible since the last call.
   void take_done(std::vector<RingDone>& out);
@@ -92,6 +95,11 @@ class RingLoop {
 
  private:
   void release();
+  void enqueue();               // the launches of one iteration
+  cudaGraphExec_t graph_[2] = {nullptr, nullptr};  // iteration launches by pass parity
+  uint64_t graph_launches_[2] = {0, 0};            // kernels each graph holds
+  uint64_t iters_ = 0;
+  bool graphs_off_ = false;     // capture failed once: launch directly
   Graph& g_;
   int B_;
   cudaStream_t st_;
