@@ -106,24 +106,39 @@ __device__ __forceinline__ void bwait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// SB bytes from global to shared memory in 16-byte cp.async copies.
+// Byte offset of 16-byte piece h inside this lane's SB-byte ring slot.  The
+// 8 lanes of a quarter-warp read piece h of their slots with one 16-byte
+// shared load; with the pieces in order, slots 32 or 64 bytes apart put
+// several of those lanes on the same banks.  So with SB = 32 lanes 4-7 (of
+// every 8) swap their two pieces, and with SB = 64 the four pieces rotate by
+// (lane / 2) % 4: each lane of a quarter-warp then reads a different 16-byte
+// bank group, and a slot still holds its own SB bytes.
+template <int SB>
+__device__ __forceinline__ uint32_t piece(int h) {
+  if constexpr (SB == 32) return (uint32_t)(16 * h) ^ (((threadIdx.x >> 2) & 1u) << 4);
+  else if constexpr (SB == 64) return 16u * ((uint32_t)h ^ ((threadIdx.x >> 1) & 3u));
+  else return 16u * (uint32_t)h;
+}
+
+// SB bytes from global to shared memory in 16-byte cp.async copies: global
+// piece h of the segment goes to piece(h) of the slot.
 template <int SB>
 __device__ __forceinline__ void cp_seg(uint32_t dst, const unsigned char* src) {
   if constexpr (SB == 16) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
   } else if constexpr (SB == 32) {
     asm volatile(
-        "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
-        "cp.async.cg.shared.global [%0+16], [%1+16], 16;" ::"r"(dst),
-        "l"(src)
+        "cp.async.cg.shared.global [%0], [%2], 16;\n\t"
+        "cp.async.cg.shared.global [%1], [%2+16], 16;" ::"r"(dst + piece<32>(0)),
+        "r"(dst + piece<32>(1)), "l"(src)
         : "memory");
   } else {
     asm volatile(
-        "cp.async.cg.shared.global [%0], [%1], 16;\n\t"
-        "cp.async.cg.shared.global [%0+16], [%1+16], 16;\n\t"
-        "cp.async.cg.shared.global [%0+32], [%1+32], 16;\n\t"
-        "cp.async.cg.shared.global [%0+48], [%1+48], 16;" ::"r"(dst),
-        "l"(src)
+        "cp.async.cg.shared.global [%0], [%4], 16;\n\t"
+        "cp.async.cg.shared.global [%1], [%4+16], 16;\n\t"
+        "cp.async.cg.shared.global [%2], [%4+32], 16;\n\t"
+        "cp.async.cg.shared.global [%3], [%4+48], 16;" ::"r"(dst + piece<64>(0)),
+        "r"(dst + piece<64>(1)), "r"(dst + piece<64>(2)), "r"(dst + piece<64>(3)), "l"(src)
         : "memory");
   }
 }
@@ -144,8 +159,11 @@ struct Store<float> {
   struct Raw {
     float4 a, b;
   };
-  __device__ static __forceinline__ Raw lds(const unsigned char* p) {
-    return Raw{*reinterpret_cast<const float4*>(p), *reinterpret_cast<const float4*>(p + 16)};
+  // pieces h and h + 1 of an SB-byte ring slot
+  template <int SB>
+  __device__ static __forceinline__ Raw lds(const unsigned char* p, int h) {
+    return Raw{*reinterpret_cast<const float4*>(p + piece<SB>(h)),
+               *reinterpret_cast<const float4*>(p + piece<SB>(h + 1))};
   }
   __device__ static __forceinline__ void add(const Raw& r, float acc[8]) {
     acc[0] += r.a.x; acc[1] += r.a.y; acc[2] += r.a.z; acc[3] += r.a.w;
@@ -175,7 +193,11 @@ struct Store<__nv_bfloat16> {
   template <int N>
   __device__ static __forceinline__ void finish(float*) {}  // sums are in Q units
   using Raw = uint4;
-  __device__ static __forceinline__ Raw lds(const unsigned char* p) { return *reinterpret_cast<const uint4*>(p); }
+  // piece h of an SB-byte ring slot
+  template <int SB>
+  __device__ static __forceinline__ Raw lds(const unsigned char* p, int h) {
+    return *reinterpret_cast<const uint4*>(p + piece<SB>(h));
+  }
   // acc += each bf16 value, widened exactly inside a mixed-precision FP32 add.
   __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
@@ -220,7 +242,11 @@ template <>
 struct Store<__half> {
   static constexpr int bytes = 2;
   using Raw = uint4;
-  __device__ static __forceinline__ Raw lds(const unsigned char* p) { return *reinterpret_cast<const uint4*>(p); }
+  // piece h of an SB-byte ring slot
+  template <int SB>
+  __device__ static __forceinline__ Raw lds(const unsigned char* p, int h) {
+    return *reinterpret_cast<const uint4*>(p + piece<SB>(h));
+  }
   // acc += each stored value (Q * 2^12), widened exactly inside a
   // mixed-precision FP32 add; finish() removes the 2^12 once per row.
   __device__ static __forceinline__ void add(const Raw& w, float acc[8]) {
@@ -370,8 +396,10 @@ __device__ __forceinline__ const unsigned char* own_src(const Lane& L, int64_t u
 // Add one gathered segment (LC values of TG) from a ring slot.
 template <typename TG, int LC>
 __device__ __forceinline__ void add_seg(const unsigned char* p, float acc[LC]) {
+  constexpr int SB = LC * Store<TG>::bytes;
+  constexpr int PG = 8 * Store<TG>::bytes / 16;  // pieces of 8 values
 #pragma unroll
-  for (int h = 0; h < LC / 8; ++h) Store<TG>::add(Store<TG>::lds(p + h * 8 * Store<TG>::bytes), acc + 8 * h);
+  for (int h = 0; h < LC / 8; ++h) Store<TG>::add(Store<TG>::template lds<SB>(p, h * PG), acc + 8 * h);
 }
 
 // A lane's neighbour sums.  FP32 gathers add in two levels: rounds go into
@@ -430,21 +458,20 @@ __device__ __forceinline__ int tile_len(const BTile& t) { return t.kind == 2 ? t
 // C0 + PC - 1) turns acc into r = 2 acc - d Q_{k-1} and writes
 // Q_{k+1} = r / d; a y piece (columns C0 .. C0 + PW - 1) adds c r to y.
 // Retired columns keep their values (Q copied, y final).
-template <typename TP, typename TO, int LC, int PC, int C0>
+template <typename TP, typename TO, int LC, int SB, int PC, int C0>
 __device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, const unsigned char* src, float acc[LC],
                                            float nrm[LC]) {
   float prev[PC];
   if constexpr (Store<TP>::bytes == 4) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
     for (int q = 0; q < PC / 4; ++q) {
-      const float4 x = s4[q];
+      const float4 x = *reinterpret_cast<const float4*>(src + piece<SB>(q));
       prev[4 * q] = x.x; prev[4 * q + 1] = x.y; prev[4 * q + 2] = x.z; prev[4 * q + 3] = x.w;
     }
   } else {
     static_assert(PC % 8 == 0, "a 16-bit Q_{k-1} segment is one round of whole 8-column groups");
 #pragma unroll
-    for (int h = 0; h < PC / 8; ++h) Store<TP>::decode(Store<TP>::lds(src + 16 * h), prev + 8 * h);
+    for (int h = 0; h < PC / 8; ++h) Store<TP>::decode(Store<TP>::template lds<SB>(src, h), prev + 8 * h);
   }
   const float inv = 1.0f / d;
   float out[PC];
@@ -484,13 +511,12 @@ __device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, co
   }
 }
 
-template <int LC, int PW, int C0>
+template <int LC, int SB, int PW, int C0>
 __device__ __forceinline__ void y_piece(const Lane& L, int64_t u, const unsigned char* src, const float acc[LC]) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
   float4* yrow = reinterpret_cast<float4*>(L.yseg + (uint64_t)(uint32_t)u * L.rowY + C0 * 4);
 #pragma unroll
   for (int q = 0; q < PW / 4; ++q) {
-    float4 x = s4[q];
+    float4 x = *reinterpret_cast<const float4*>(src + piece<SB>(q));
     float* xv = reinterpret_cast<float*>(&x);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -509,21 +535,21 @@ __device__ __forceinline__ void own_round(const Lane& L, int64_t u, float d, int
   constexpr int PC = LC / OP, PW = LC / OY;
   if (o < OP) {
     if constexpr (OP == 1) {
-      prev_piece<TP, TO, LC, PC, 0>(L, u, d, src, acc, nrm);
+      prev_piece<TP, TO, LC, SB, PC, 0>(L, u, d, src, acc, nrm);
     } else {
       if (o == 0)
-        prev_piece<TP, TO, LC, PC, 0>(L, u, d, src, acc, nrm);
+        prev_piece<TP, TO, LC, SB, PC, 0>(L, u, d, src, acc, nrm);
       else
-        prev_piece<TP, TO, LC, PC, PC>(L, u, d, src, acc, nrm);
+        prev_piece<TP, TO, LC, SB, PC, PC>(L, u, d, src, acc, nrm);
     }
   } else {
     if constexpr (OY == 1) {
-      y_piece<LC, PW, 0>(L, u, src, acc);
+      y_piece<LC, SB, PW, 0>(L, u, src, acc);
     } else {
       if (o == OP)
-        y_piece<LC, PW, 0>(L, u, src, acc);
+        y_piece<LC, SB, PW, 0>(L, u, src, acc);
       else
-        y_piece<LC, PW, PW>(L, u, src, acc);
+        y_piece<LC, SB, PW, PW>(L, u, src, acc);
     }
   }
 }
