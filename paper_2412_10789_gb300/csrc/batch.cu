@@ -361,7 +361,7 @@ struct Geo {
 // each copy.
 struct Lane {
   const SpmmArgs* a;            // (chunk and finisher paths only)
-  const ColState* s_col;        // state of this lane's first column
+  const ColState* s_col;        // state of this lane's column c at s_col[c * CG] (col())
   uint32_t ring;                // shared address of this lane's slot 0
   const unsigned char* ring_p;  // the same, generic
   const unsigned char* qseg;    // Q_k + this lane's segment offset
@@ -374,6 +374,7 @@ struct Lane {
   int mode;                     // kMode*: which row update the pass applies
   int B;                        // columns of this pass
   int cg, g, CG, EG, lane;
+  __device__ __forceinline__ ColState col(int c) const { return s_col[c * CG]; }
 };
 
 // Source of the gathered segment of neighbour v.  Rows beyond the active ones,
@@ -490,7 +491,7 @@ __device__ __forceinline__ void prev_piece(const Lane& L, int64_t u, float d, co
 #pragma unroll
   for (int i = 0; i < PC; ++i) {
     const int c = C0 + i;
-    const ColState cs = L.s_col[c];
+    const ColState cs = L.col(c);
     const float r = two * acc[c] - dp * prev[i];
     out[i] = cs.active ? r * inv : prev[i];
     acc[c] = cs.active ? r : 0.f;
@@ -521,7 +522,7 @@ __device__ __forceinline__ void y_piece(const Lane& L, int64_t u, const unsigned
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int c = C0 + 4 * q + k;
-      const ColState cs = L.s_col[c];
+      const ColState cs = L.col(c);
       xv[k] = fmaf(cs.active ? cs.coef : 0.f, acc[c], xv[k]);
     }
     yrow[q] = x;
@@ -667,7 +668,7 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int c = 8 * h + i;
-        const ColState cs = L.s_col[c];
+        const ColState cs = L.col(c);
         const float r = first ? tot[c] : 2.0f * tot[c] - d * pv.x[i];
         out.x[i] = cs.active ? r * inv : pv.x[i];
         tot[c] = cs.active ? r : 0.f;
@@ -683,7 +684,7 @@ __device__ __forceinline__ void finish_long_row(const Lane& L, int64_t row, int 
       float* xv = reinterpret_cast<float*>(&x);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const ColState cs = L.s_col[4 * q + k];
+        const ColState cs = L.col(4 * q + k);
         xv[k] = fmaf(cs.active ? cs.coef : 0.f, tot[4 * q + k], xv[k]);
       }
       yrow[q] = x;
@@ -858,8 +859,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   unsigned char* ring = s_raw + kHeaderBytes + (size_t)warp * 32 * kRingLaneBytes;
   int* s_ci = reinterpret_cast<int*>(s_raw + kHeaderBytes + (size_t)kBatchWarps * 32 * kRingLaneBytes) +
               warp * 2 * kBTileSpan;
+  // column j = cg * LC + i of the pass is stored at i * CG + cg, so that the
+  // lane groups of a warp reading column i of their segments read adjacent
+  // entries (in column order the reads were LC * 8 bytes apart: one bank)
   for (int j = threadIdx.x; j < B; j += blockDim.x) {
-    s_col[j] = a.col[j];
+    s_col[(j % LC) * (B / LC) + j / LC] = a.col[j];
     s_norm[j] = 0.f;
   }
   __syncthreads();
@@ -871,7 +875,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) spmm_step_kernel(const __gri
   L.cg = lane % L.CG;
   L.g = lane / L.CG;
   L.lane = lane;
-  L.s_col = s_col + L.cg * LC;
+  L.s_col = s_col + L.cg;
   L.ring = (uint32_t)__cvta_generic_to_shared(ring) + lane * C::SB;
   L.ring_p = ring + lane * C::SB;
   L.qseg = static_cast<const unsigned char*>(a.qcur) + (size_t)L.cg * C::SB;
