@@ -16,6 +16,15 @@ fused step kernel's algorithmic bytes per launch over its mean CUDA-event
 duration, against the measured HBM copy bandwidth.  `cpu_baseline` times the
 FP64 oracle on the host cores on a bounded sample of the same workload.
 
+On the same graph and queries the line also carries `gpu_power_baseline`
+(Algorithm 1 on the GPU). `batched` holds 128-column blocks in BF16 and FP16
+at l1 1e-4, and FP32 at 1e-6 and 1e-4, plus Clenshaw's form. The served legs
+go through gp_submit / gp_poll: FP32 and BF16 services on mixed tolerances,
+and BF16 and FP16 services at l1 1e-4, each saturated and under Poisson
+arrivals at 50/80/95 % of that rate, with p50/p99 latency. The client keeps
+every slot busy: a 16-bit service has two blocks. `errors_vs_oracle` gives
+the l1 and max-abs of sampled outputs of every result against the oracle.
+
 Multi-GPU: queries are independent, so N GPUs run N replicas of the graph
 with the same per-GPU work (weak scaling, no data-path collective).
 `--impl reference` times the FP64 oracle on the host cores instead.
